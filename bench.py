@@ -1,0 +1,349 @@
+"""Benchmark of the exact-SRE hot path (and its CPU oracle as the reference arm).
+
+Default workload (one step = one complete exact M_2 of one state, every X-string):
+  N = 20 qubits, complex64 state of a seeded brick-wall circuit of Haar-random two-qubit
+  gates on |0...0> (depth 10, open chain, seed 2001 -- the paper's Eq. randC workload),
+  FP32 CUDA-core Walsh-Hadamard path, 4^20 = 1.1e12 Pauli strings per step.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+                  [--N 20] [--path cudacore|tensor] [--no-cpu-baseline] [--extra]
+
+Multi-GPU (torchrun, one rank per GPU): the X-strings are independent (Sec. 3.1.2), so every
+rank runs the same per-state work on its own replica ("scaling": "weak", no collective on
+the data path); rank 0 prints the JSON line with the max time over ranks.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Pauli strings/s for exact SRE (N=20,22 qubits) & mana (N=11); % of roofline"
+UNIT = "Pauli strings/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--N", type=int, default=20)
+    ap.add_argument("--path", default="cudacore", choices=["cudacore", "tensor", "auto"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--extra", action="store_true", help="also time N=22, mana N=11, MC N=28, batched")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def workload_state(N: int):
+    import numpy as np
+    from paper_2601_07824_gb300 import inputs
+    if N == 20:
+        return inputs.brickwork_haar(20, 10, seed=2001, dtype=np.complex64), \
+            "brickwork Haar circuit on |0>^20, depth 10, open chain, seed 2001"
+    return inputs.brickwork_haar(N, 10, seed=2000 + N, dtype=np.complex64), \
+        f"brickwork Haar circuit on |0>^{N}, depth 10, open chain, seed {2000 + N}"
+
+
+def ops_per_string(N: int) -> int:
+    # FP32 operations per Pauli string (FMA counted once) in the half-length form:
+    # (N-1) butterfly stages, 2 for the pair product, 3 for the |c|^4 and |c|^2 reduction.
+    return N + 4
+
+
+def fp32_peak_ops(sm_count: int, mhz: float) -> float:
+    return sm_count * 128 * mhz * 1e6
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled every 200 ms while running."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+        self.t = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *exc):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.t.join(timeout=2)
+
+    def summary(self):
+        mhz, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                mhz.append(float(parts[1]))
+                mx = float(parts[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not mhz:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(mhz), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(mhz)}
+
+
+def _calibrate(oracle, psi_np, dim, threads, rng):
+    """Seconds per X-string of the oracle on this host (probe grown until it takes >= 0.3 s)."""
+    count = max(threads, 4)
+    while True:
+        probe = rng.integers(0, dim, count)
+        t0 = time.perf_counter()
+        oracle.sre_terms_list(psi_np, probe, threads)
+        dt = time.perf_counter() - t0
+        if dt >= 0.3 or count >= (1 << 20):
+            return dt / count
+        count *= 4
+
+
+def cpu_baseline(psi_np, N: int, seconds: float):
+    """The FP64 oracle (as it stands) on a bounded sample of X-strings of the same workload."""
+    import numpy as np
+    import oracle
+    threads = oracle.num_threads(0)
+    dim = 2 ** N
+    rng = np.random.default_rng(12345)
+    # calibrate on a handful of X-strings, then size the sample to ~`seconds` of CPU work
+    per_a = _calibrate(oracle, psi_np, dim, threads, rng)
+    count = int(max(threads, min(1 << 22, seconds / max(per_a, 1e-9))))
+    a = rng.integers(0, dim, count)
+    t0 = time.perf_counter()
+    oracle.sre_terms_list(psi_np, a, threads)
+    dt = time.perf_counter() - t0
+    return {"value": count * dim / dt, "unit": UNIT, "cores": threads, "kind": "oracle",
+            "sample": f"{count} uniformly drawn X-strings of the N={N} workload (each a full "
+                      f"2^{N}-point FP64 Walsh-Hadamard transform), {dt:.1f} s"}, dt
+
+
+def run_reference(args):
+    """--impl reference: the FP64 CPU oracle timed on this host, same metric and config."""
+    import numpy as np
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    import oracle
+    N = args.N
+    psi, desc = workload_state(N)
+    threads = oracle.num_threads(0)
+    dim = 2 ** N
+    rng = np.random.default_rng(777)
+    per_a = _calibrate(oracle, psi, dim, threads, rng)
+    budget = max(2.0, 120.0 / max(1, args.steps + args.warmup))
+    count = int(max(threads, budget / max(per_a, 1e-9)))
+    times = []
+    for s in range(args.warmup + args.steps):
+        a = rng.integers(0, dim, count)
+        t0 = time.perf_counter()
+        oracle.sre_terms_list(psi, a, threads)
+        if s >= args.warmup:
+            times.append(time.perf_counter() - t0)
+    total = sum(times)
+    value = args.steps * count * dim / total
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": f"exact M2, N={N}: {desc}; complex64 amplitudes read in FP64",
+                   "N": N, "n": 2, "step": f"{count} X-strings (bounded sample of the 2^{N})"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
+                         "sample": f"{count} X-strings per step, {args.steps} timed steps"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return run_reference(args)
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device(f"cuda:{local}"))
+    dev = torch.device(f"cuda:{local}")
+    torch.cuda.set_device(dev)
+
+    import paper_2601_07824_gb300 as hm
+    from paper_2601_07824_gb300 import _lib
+
+    N = args.N
+    psi_np, desc = workload_state(N)
+    psi = torch.from_numpy(psi_np).to(dev)
+    ctx = _lib.context(local)
+    path = {"cudacore": _lib.PATH_CUDACORE, "tensor": _lib.PATH_TENSOR, "auto": _lib.PATH_AUTO}[args.path]
+    ctx.set_path(path)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+    stream = torch.cuda.current_stream(dev)
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize(dev)
+
+    M = None
+    for _ in range(args.warmup):
+        M, ln = hm.sre(psi, 2.0)
+    barrier()
+    launches0 = ctx.launch_count()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+          for _ in range(args.steps)]
+    with ClockSampler(local) as clk:
+        for s in range(args.steps):
+            flush.fill_(s & 0xFF)  # evict L2 between steps (the state is smaller than L2)
+            ev[s][0].record(stream)
+            M, ln = hm.sre(psi, 2.0)
+            ev[s][1].record(stream)
+        barrier()
+    launches = ctx.launch_count() - launches0
+    step_ms = [a.elapsed_time(b) for a, b in ev]
+    t_local = sum(step_ms) / 1e3
+    t = torch.tensor([t_local], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_max = float(t.item())
+    strings_per_step = 4.0 ** N
+    value = world * args.steps * strings_per_step / t_max
+    clocks = clk.summary()
+
+    # end-to-end: the C-ABI host-buffer call, H2D copy from pinned memory inside the timed region
+    e2e = None
+    if not args.no_e2e:
+        host = torch.from_numpy(psi_np).pin_memory()
+        hm.sre_host(host.numpy(), 2.0, device=local)
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            hm.sre_host(host.numpy(), 2.0, device=local)
+        barrier()
+        te = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
+        if world > 1:
+            dist.all_reduce(te, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * args.steps * strings_per_step / float(te.item()), "unit": UNIT,
+               "h2d_bytes_per_step": int(psi_np.nbytes), "d2h_bytes_per_step": 3 * 8 + 4}
+
+    line = None
+    if rank == 0:
+        ops = ops_per_string(N) * strings_per_step
+        avg_s = t_local / args.steps
+        achieved = ops / avg_s
+        mhz_max = 2070.0
+        peak = fp32_peak_ops(sm_count, mhz_max)
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"exact M2, N={N}: {desc}; complex64; FP32 {args.path} Walsh-Hadamard path",
+                       "N": N, "n": 2, "strings_per_step": strings_per_step,
+                       "l2": "state (8 MiB) is smaller than L2: a 256 MiB buffer is written between steps",
+                       "M2": M, "lost_norm": ln},
+            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "note": f"FP32 ops (FMA = 1) = {ops_per_string(N)} per Pauli string; peak = "
+                                 f"{sm_count} SMs x 128 lanes x {mhz_max:.0f} MHz; kernel time = CUDA events "
+                                 "around the call on its stream"},
+            "clocks": clocks,
+            "gpu_launches": launches,
+            "e2e": e2e,
+        }
+        if clocks.get("sm_mhz"):
+            line["roofline"]["frac_at_measured_clock"] = achieved / fp32_peak_ops(sm_count, clocks["sm_mhz"])
+    if world > 1:
+        dist.barrier()
+    if rank == 0 and not args.no_cpu_baseline:
+        cb, _ = cpu_baseline(psi_np, N, args.cpu_seconds)
+        line["cpu_baseline"] = cb
+    if rank == 0 and args.extra:
+        line["extra"] = extra_workloads(hm, dev, sm_count)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def extra_workloads(hm, dev, sm_count):
+    """Other configurations, one timed call each (not part of the headline value)."""
+    import numpy as np
+    import torch
+    from paper_2601_07824_gb300 import _lib, inputs
+    out = {}
+
+    def timed(fn, reps=1):
+        fn()
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            r = fn()
+        torch.cuda.synchronize(dev)
+        return (time.perf_counter() - t0) / reps, r
+
+    ctx = _lib.context(dev.index or 0)
+    psi22 = torch.from_numpy(inputs.gaussian_state(22, 2201, dtype=np.complex64)).to(dev)
+    for name, p in (("cudacore", _lib.PATH_CUDACORE), ("tensor", _lib.PATH_TENSOR)):
+        try:
+            ctx.set_path(p)
+            dt, r = timed(lambda: hm.sre(psi22, 2.0))
+            out[f"sre_N22_{name}"] = {"strings_per_s": 4.0 ** 22 / dt, "s": dt, "M2": r[0]}
+        except Exception as e:  # noqa: BLE001
+            out[f"sre_N22_{name}"] = {"error": str(e)}
+    ctx.set_path(_lib.PATH_CUDACORE)
+    try:
+        q = torch.from_numpy(inputs.gaussian_state(11, 1101, d=3, dtype=np.complex64)).to(dev)
+        dt, r = timed(lambda: hm.mana(q), reps=5)
+        out["mana_N11"] = {"points_per_s": 9.0 ** 11 / dt, "s": dt, "mana": r[0]}
+    except Exception as e:  # noqa: BLE001
+        out["mana_N11"] = {"error": str(e)}
+    return out
+
+
+if __name__ == "__main__":
+    main()

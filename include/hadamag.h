@@ -1,0 +1,166 @@
+/*
+ * hadamag.h -- C ABI of libhadamag: magic (non-stabilizerness) of state vectors on one
+ * NVIDIA GB300 GPU (sm_103a), following "Computing quantum magic of state vectors"
+ * (arXiv 2601.07824).
+ *
+ * Conventions shared by every call
+ *   - A qubit state has 2^N amplitudes, a qutrit state 3^N; site j is digit j of the index
+ *     (least significant first).  Amplitudes are interleaved (re, im): HADAMAG_C64 = two
+ *     floats, HADAMAG_C128 = two doubles.  Device pointers must be 16-byte aligned.
+ *   - States are NOT renormalised: every quantity is the paper's formula evaluated on the
+ *     vector as given; lost_norm reports 1 - sum_P <P>^2 / 2^N (Sec. 4.1).
+ *   - Ownership: every pointer belongs to the caller; the library never frees or keeps it
+ *     after the call returns.  Scratch memory belongs to the context and is reused.
+ *   - Ordering: work is enqueued on the caller's CUDA stream (NULL = legacy default
+ *     stream).  Calls that return host values synchronise that stream before returning.
+ *     A context is not thread-safe: use one per host thread.
+ *   - Errors: every call returns a status code; nothing aborts, throws or traps.  Invalid
+ *     arguments return HADAMAG_ERR_INVALID_ARG before any work is enqueued.
+ *   - Precision: transforms run in FP32 (CUDA-core path) or on FP16 hi/lo tensor-core
+ *     operands with FP32 accumulation (tensor path); every cross-tile sum and the final
+ *     logarithm are FP64.  HADAMAG_C128 input is rounded to FP32 on the device first.
+ */
+#ifndef HADAMAG_H
+#define HADAMAG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    HADAMAG_OK = 0,
+    HADAMAG_ERR_INVALID_ARG = 1, /* bad N, n, count, null or misaligned pointer, bad list entry */
+    HADAMAG_ERR_UNSUPPORTED = 2, /* valid request outside what this build implements */
+    HADAMAG_ERR_OOM = 3,         /* device or pinned allocation failed */
+    HADAMAG_ERR_CUDA = 4,        /* a CUDA runtime call failed (see hadamag_last_error) */
+    HADAMAG_ERR_TIMEOUT = 5,     /* a bounded inter-CTA wait ran out; the launch stopped early */
+    HADAMAG_ERR_NONFINITE = 6    /* the result is NaN or infinite (non-finite input) */
+} hadamag_status;
+
+typedef enum { HADAMAG_C64 = 0, HADAMAG_C128 = 1 } hadamag_dtype;
+
+typedef enum {
+    HADAMAG_PATH_AUTO = 0,     /* the library picks */
+    HADAMAG_PATH_CUDACORE = 1, /* FP32 butterflies on CUDA cores */
+    HADAMAG_PATH_TENSOR = 2    /* +-1 Hadamard blocks on tcgen05 tensor cores, FP16 hi/lo operands */
+} hadamag_path;
+
+typedef struct hadamag_ctx_s* hadamag_ctx_t;
+typedef struct CUstream_st* hadamag_stream_t; /* same type as cudaStream_t */
+
+/* Create a context on `device` (CUDA ordinal).  Owns scratch buffers, a status word and a
+ * private stream used by the host-buffer variants.  Returns INVALID_ARG for a null ctx
+ * pointer or a bad ordinal, OOM/CUDA on failure. */
+hadamag_status hadamag_create(hadamag_ctx_t* ctx, int device);
+/* Free everything the context owns.  Null is accepted. */
+hadamag_status hadamag_destroy(hadamag_ctx_t ctx);
+/* Choose the transform path for later calls (default AUTO). */
+hadamag_status hadamag_set_path(hadamag_ctx_t ctx, hadamag_path path);
+/* Bound of every inter-CTA wait, in polling iterations (~0.1 us each; default 2^25), and a
+ * value added to every wait target.  A non-zero bias makes waits unsatisfiable; it exists
+ * only so tests can check that a wait that runs out returns HADAMAG_ERR_TIMEOUT. */
+hadamag_status hadamag_set_wait_limit(hadamag_ctx_t ctx, long long spins, unsigned bias);
+/* Number of kernel launches this context has issued since creation. */
+hadamag_status hadamag_launch_count(hadamag_ctx_t ctx, uint64_t* count);
+const char* hadamag_status_string(hadamag_status s);
+/* Text of the last error recorded on this context ("" if none). */
+const char* hadamag_last_error(hadamag_ctx_t ctx);
+
+/*
+ * Exact stabilizer Renyi entropy, Eq. (sre) of Sec. 2, evaluated by the per-X-string
+ * Walsh-Hadamard method of Sec. 3.1.2 (Algorithm 2):
+ *     M_n = 1/(1-n) log2( sum_{a,b} |<psi|X_a Z_b|psi>|^{2n} / 2^N ),
+ *     M_1 = -sum_P pi_P log2 pi_P - N with pi_P = <P>^2 / sum_P <P>^2 (limit n -> 1),
+ *     lost_norm = 1 - sum_P <P>^2 / 2^N (Sec. 4.1).
+ * psi_dev: 2^N amplitudes on the device.  1 <= N <= 24, n > 0 (n = 1, 2, 3 have dedicated
+ * kernels; other n accumulate exp2(n log2 |c|^2) in FP64).  M_out and lost_norm_out are host
+ * pointers (lost_norm_out may be NULL).  Synchronises `stream`.
+ */
+hadamag_status hadamag_sre(hadamag_ctx_t ctx, const void* psi_dev, int N, double n,
+                           hadamag_dtype dtype, double* M_out, double* lost_norm_out,
+                           hadamag_stream_t stream);
+
+/* Same as hadamag_sre with psi in HOST memory: the call copies it to the device on the
+ * context's own stream (inside the call), computes, and returns host results. */
+hadamag_status hadamag_sre_host(hadamag_ctx_t ctx, const void* psi_host, int N, double n,
+                                hadamag_dtype dtype, double* M_out, double* lost_norm_out);
+
+/*
+ * Per-X-string sums of Algorithm 2 for an explicit list of X-strings:
+ *     terms_dev[3i+0] = sum_b |chi_b(a_i)|^{2n},  terms_dev[3i+1] = sum_b |chi_b(a_i)|^2,
+ *     terms_dev[3i+2] = sum_b |chi_b|^2 log2 |chi_b|^2 (n = 1 only, else 0),
+ * with chi_b(a) = <psi| X_a Z_b |psi> (Eq. Z_FT_qubits).  a_list_dev: `count` int64 entries
+ * in [0, 2^N) on the device (an entry outside gives INVALID_ARG after the launch and its
+ * terms are left unwritten).  terms_dev: count*3 doubles on the device.  Stream-ordered;
+ * synchronises `stream` to read the status word.
+ */
+hadamag_status hadamag_sre_terms(hadamag_ctx_t ctx, const void* psi_dev, int N, double n,
+                                 hadamag_dtype dtype, const int64_t* a_list_dev, int64_t count,
+                                 double* terms_dev, hadamag_stream_t stream);
+
+/*
+ * X-strings of the uniform Monte-Carlo estimator: a_i = top N bits of output i of
+ * SplitMix64 (Steele, Lea & Flood 2014) started at `seed`, i = 0..count-1, written to
+ * a_out_dev (count int64 on the device).  1 <= N <= 30.  Stream-ordered, no sync.
+ */
+hadamag_status hadamag_mc_xstrings(hadamag_ctx_t ctx, uint64_t seed, int64_t count, int N,
+                                   int64_t* a_out_dev, hadamag_stream_t stream);
+
+/*
+ * Uniform-X Monte-Carlo M_2: S_hat = mean_i sum_b |chi_b(a_i)|^4 over `samples` X-strings
+ * drawn as in hadamag_mc_xstrings; M2_hat = -log2(S_hat) (an unbiased estimate of
+ * S_2 / 2^N, from the per-X decomposition of Algorithm 2); stderr_out = sd / (sqrt(samples)
+ * S_hat ln 2) (Eq. M2mNcerror).  1 <= N <= 28 (N >= 25 uses a two-pass HBM schedule).
+ * stderr_out may be NULL.  Synchronises `stream`.
+ */
+hadamag_status hadamag_sre_mc(hadamag_ctx_t ctx, const void* psi_dev, int N, int64_t samples,
+                              uint64_t seed, hadamag_dtype dtype, double* M2_out,
+                              double* stderr_out, hadamag_stream_t stream);
+
+/*
+ * Mana of an N-qutrit pure state, Eq. (mana2) of Sec. 2 evaluated by the per-X-string
+ * Z_3^N Fourier transform of Sec. 3.3.2 (Algorithm 5, Eqs. mana_FT and F3_unnorm_def):
+ *     mana = log2( sum_{a,b} |chi_b(a)| / 3^N ),  chi = F_3^{(x)N} (alpha*_x alpha_{-x}).
+ * mana_out is in bits (the paper's log2); sum_w_out = sum_u |W(u)| (so ln sum_w is the
+ * natural-log mana).  1 <= N <= 13.  Either output may be NULL.  Synchronises `stream`.
+ */
+hadamag_status hadamag_mana(hadamag_ctx_t ctx, const void* psi_dev, int N, hadamag_dtype dtype,
+                            double* mana_out, double* sum_w_out, hadamag_stream_t stream);
+
+/* Raw sums behind hadamag_mana: sums_out[0] = sum_{a,b} |chi_b(a)|, sums_out[1] = sum chi_b(a),
+ * sums_out[2] = sum chi_b(a)^2 (host doubles).  With W = chi / 3^N these give the Wigner sum
+ * rules of Sec. 2: sum_u W(u) = 1 and, for pure states, sum_u W(u)^2 = 3^-N. */
+hadamag_status hadamag_mana_sums(hadamag_ctx_t ctx, const void* psi_dev, int N, hadamag_dtype dtype,
+                                 double* sums_out, hadamag_stream_t stream);
+
+/*
+ * M_2 and its Wirtinger gradient dM_2/dpsi* (not in the paper; it is what magic
+ * optimisation of circuits needs).  With c_a = H^{(x)N} v_a as in Algorithm 2,
+ *     dS_2/dpsi*_w = sum_a psi_{w^a} [G_a(w) + conj(G_a(w^a))],  G_a = H^{(x)N}(2|c_a|^2 c_a),
+ *     dM_2/dpsi* = -dS_2/dpsi* / (ln 2 S_2).
+ * The adjoint recomputes c_a instead of storing 4^N values.  grad_dev: 2^N amplitudes of the
+ * same dtype as psi, on the device.  1 <= N <= 20.  Synchronises `stream`.
+ */
+hadamag_status hadamag_sre_grad(hadamag_ctx_t ctx, const void* psi_dev, int N, hadamag_dtype dtype,
+                                double* M2_out, void* grad_dev, hadamag_stream_t stream);
+
+/*
+ * Many states of uneven N (1 <= N_i <= 18) in one persistent launch: M_2 of each into
+ * M2_dev[i] (device doubles) and, if want_grad, dM_2/dpsi* into grad_dev[i].  psi_dev and
+ * grad_dev are HOST arrays of `count` device pointers (complex64 only).  Work is split into
+ * (state, X-string chunk) items scheduled largest first; chunk sizes come from the
+ * context's autotuner.  Stream-ordered; no host sync, so it can be captured in a CUDA graph
+ * after one uncaptured warm-up call with the same shapes.
+ */
+hadamag_status hadamag_sre_batched(hadamag_ctx_t ctx, int count, const void* const* psi_dev,
+                                   const int* N, int want_grad, void* const* grad_dev,
+                                   double* M2_dev, hadamag_stream_t stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HADAMAG_H */

@@ -1,0 +1,25 @@
+"""GB300-native magic (non-stabilizerness) of state vectors.
+
+Implements the hot path of "Computing quantum magic of state vectors" (arXiv 2601.07824):
+the exact stabilizer Renyi entropy M_n (Algorithm 2: one Walsh-Hadamard transform per
+X-string), the qutrit mana (Algorithm 5: one Z_3^N Fourier transform per X-string), a
+uniform-X Monte-Carlo M_2, the Wirtinger gradient dM_2/dpsi*, and a batched persistent
+launch over many states.  All arithmetic runs in hand-written sm_103a CUDA kernels in
+libhadamag.so behind a C ABI (include/hadamag.h); this package only marshals PyTorch CUDA
+tensors into that ABI.
+
+`paper_2601_07824_gb300.inputs` (seeded synthetic states) imports no CUDA code.
+"""
+from __future__ import annotations
+
+__all__ = ["sre", "sre_host", "sre_terms", "mc_xstrings", "sre_mc", "mana", "mana_sums", "sre_grad",
+           "SREFunction", "sre_batched", "context", "HadamagError", "PATH_AUTO",
+           "PATH_CUDACORE", "PATH_TENSOR"]
+
+
+def __getattr__(name):
+    # The binding (and torch) load lazily so that `inputs` stays importable without them.
+    if name in __all__:
+        from . import api
+        return getattr(api, name)
+    raise AttributeError(name)

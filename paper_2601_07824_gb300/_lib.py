@@ -1,0 +1,132 @@
+"""ctypes binding of libhadamag.so (C ABI in include/hadamag.h).
+
+Argument marshalling only: every step of the computation runs in the library's CUDA
+kernels.  There is no CPU fallback: if the shared library is missing or no GPU is present,
+calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libhadamag.so")
+
+C64, C128 = 0, 1
+PATH_AUTO, PATH_CUDACORE, PATH_TENSOR = 0, 1, 2
+
+STATUS = {0: "ok", 1: "invalid argument", 2: "unsupported", 3: "out of memory", 4: "CUDA error",
+          5: "device wait timed out", 6: "non-finite result"}
+
+EXPORTS = [
+    "hadamag_create", "hadamag_destroy", "hadamag_set_path", "hadamag_set_wait_limit",
+    "hadamag_launch_count", "hadamag_status_string", "hadamag_last_error", "hadamag_sre",
+    "hadamag_sre_host", "hadamag_sre_terms", "hadamag_mc_xstrings", "hadamag_sre_mc",
+    "hadamag_mana", "hadamag_mana_sums", "hadamag_sre_grad", "hadamag_sre_batched",
+]
+
+
+class HadamagError(RuntimeError):
+    def __init__(self, code: int, where: str, detail: str = ""):
+        self.code = code
+        msg = f"{where}: {STATUS.get(code, code)}"
+        if detail:
+            msg += f" ({detail})"
+        super().__init__(msg)
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def load(path: str | None = None):
+    """Load libhadamag.so (built in-tree by `paper_2601_07824_gb300.build`)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        p = path or LIB_PATH
+        if not os.path.exists(p):
+            raise ImportError(f"{p} is missing: build it with `python -m paper_2601_07824_gb300.build` "
+                              "(the CUDA library is required; there is no CPU fallback)")
+        lib = ctypes.CDLL(p)
+        V, I, D, L, U64 = ctypes.c_void_p, ctypes.c_int, ctypes.c_double, ctypes.c_int64, ctypes.c_uint64
+        PD, PV = ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_void_p)
+        sig = {
+            "hadamag_create": [ctypes.POINTER(V), I],
+            "hadamag_destroy": [V],
+            "hadamag_set_path": [V, I],
+            "hadamag_set_wait_limit": [V, ctypes.c_longlong, ctypes.c_uint],
+            "hadamag_launch_count": [V, ctypes.POINTER(U64)],
+            "hadamag_status_string": [I],
+            "hadamag_last_error": [V],
+            "hadamag_sre": [V, V, I, D, I, PD, PD, V],
+            "hadamag_sre_host": [V, V, I, D, I, PD, PD],
+            "hadamag_sre_terms": [V, V, I, D, I, V, L, V, V],
+            "hadamag_mc_xstrings": [V, U64, L, I, V, V],
+            "hadamag_sre_mc": [V, V, I, L, U64, I, PD, PD, V],
+            "hadamag_mana": [V, V, I, I, PD, PD, V],
+            "hadamag_mana_sums": [V, V, I, I, PD, V],
+            "hadamag_sre_grad": [V, V, I, I, PD, V, V],
+            "hadamag_sre_batched": [V, I, PV, ctypes.POINTER(I), I, PV, V, V],
+        }
+        for name, args in sig.items():
+            f = getattr(lib, name)
+            f.argtypes = args
+            f.restype = ctypes.c_char_p if name in ("hadamag_status_string", "hadamag_last_error") else I
+        _lib = lib
+        return lib
+
+
+class Context:
+    """Owns one hadamag_ctx_t on one CUDA device."""
+
+    def __init__(self, device: int = 0):
+        self.lib = load()
+        self.device = device
+        h = ctypes.c_void_p()
+        rc = self.lib.hadamag_create(ctypes.byref(h), int(device))
+        if rc != 0:
+            raise HadamagError(rc, "hadamag_create", f"device {device}")
+        self.h = h
+
+    def check(self, rc: int, where: str):
+        if rc != 0:
+            detail = self.lib.hadamag_last_error(self.h)
+            raise HadamagError(rc, where, detail.decode() if detail else "")
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.hadamag_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def launch_count(self) -> int:
+        n = ctypes.c_uint64()
+        self.check(self.lib.hadamag_launch_count(self.h, ctypes.byref(n)), "hadamag_launch_count")
+        return n.value
+
+    def set_path(self, path: int):
+        self.check(self.lib.hadamag_set_path(self.h, int(path)), "hadamag_set_path")
+
+    def set_wait_limit(self, spins: int, bias: int = 0):
+        self.check(self.lib.hadamag_set_wait_limit(self.h, int(spins), int(bias)), "hadamag_set_wait_limit")
+
+
+_contexts: dict[int, Context] = {}
+
+
+def context(device: int = 0) -> Context:
+    with _lock:
+        c = _contexts.get(device)
+    if c is None:
+        c = Context(device)
+        with _lock:
+            _contexts[device] = c
+    return c

@@ -1,0 +1,184 @@
+"""PyTorch-facing calls with the C ABI's names (argument marshalling only).
+
+Tensors must be CUDA, contiguous, complex64 or complex128 (batched: complex64).  Work is
+enqueued on torch's current stream of the tensor's device.
+"""
+from __future__ import annotations
+
+import ctypes
+
+import numpy as np
+import torch
+
+from ._lib import (C64, C128, PATH_AUTO, PATH_CUDACORE, PATH_TENSOR, HadamagError, context)
+
+__all__ = ["sre", "sre_host", "sre_terms", "mc_xstrings", "sre_mc", "mana", "mana_sums", "sre_grad",
+           "SREFunction", "sre_batched", "context", "HadamagError", "PATH_AUTO",
+           "PATH_CUDACORE", "PATH_TENSOR"]
+
+
+def _dtype_code(t: torch.Tensor) -> int:
+    if t.dtype == torch.complex64:
+        return C64
+    if t.dtype == torch.complex128:
+        return C128
+    raise TypeError(f"state must be complex64 or complex128, got {t.dtype}")
+
+
+def _check_state(psi: torch.Tensor, d: int = 2) -> int:
+    if not isinstance(psi, torch.Tensor) or not psi.is_cuda:
+        raise TypeError("state must be a CUDA tensor")
+    if psi.dim() != 1 or not psi.is_contiguous():
+        raise ValueError("state must be a contiguous 1-D tensor")
+    n, size = 0, psi.numel()
+    while d ** n < size:
+        n += 1
+    if d ** n != size or n < 1:
+        raise ValueError(f"state length {size} is not {d}^N")
+    return n
+
+
+def _stream(t: torch.Tensor):
+    return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+
+
+def _ctx(t: torch.Tensor):
+    return context(t.device.index if t.device.index is not None else torch.cuda.current_device())
+
+
+def sre(psi: torch.Tensor, n: float = 2.0, path: int | None = None):
+    """(M_n, lost_norm): exact SRE, Eq. (sre), by the per-X-string Walsh-Hadamard method."""
+    N = _check_state(psi)
+    c = _ctx(psi)
+    if path is not None:
+        c.set_path(path)
+    M, ln = ctypes.c_double(), ctypes.c_double()
+    c.check(c.lib.hadamag_sre(c.h, ctypes.c_void_p(psi.data_ptr()), N, float(n), _dtype_code(psi),
+                              ctypes.byref(M), ctypes.byref(ln), _stream(psi)), "hadamag_sre")
+    return M.value, ln.value
+
+
+def sre_host(psi: np.ndarray, n: float = 2.0, device: int = 0):
+    """hadamag_sre on a HOST array (the call copies it to the device itself)."""
+    a = np.ascontiguousarray(psi)
+    if a.dtype == np.complex64:
+        code = C64
+    elif a.dtype == np.complex128:
+        code = C128
+    else:
+        raise TypeError("state must be complex64 or complex128")
+    N = int(a.size).bit_length() - 1
+    if 1 << N != a.size:
+        raise ValueError("state length must be 2^N")
+    c = context(device)
+    M, ln = ctypes.c_double(), ctypes.c_double()
+    c.check(c.lib.hadamag_sre_host(c.h, ctypes.c_void_p(a.ctypes.data), N, float(n), code,
+                                   ctypes.byref(M), ctypes.byref(ln)), "hadamag_sre_host")
+    return M.value, ln.value
+
+
+def sre_terms(psi: torch.Tensor, n: float, a_list: torch.Tensor) -> torch.Tensor:
+    """Per-X-string sums [sum_b |chi|^{2n}, sum_b |chi|^2, sum_b |chi|^2 log2 |chi|^2] (count x 3)."""
+    N = _check_state(psi)
+    if a_list.dtype != torch.int64 or a_list.device != psi.device or not a_list.is_contiguous():
+        raise ValueError("a_list must be a contiguous int64 tensor on the state's device")
+    out = torch.empty((a_list.numel(), 3), dtype=torch.float64, device=psi.device)
+    c = _ctx(psi)
+    c.check(c.lib.hadamag_sre_terms(c.h, ctypes.c_void_p(psi.data_ptr()), N, float(n), _dtype_code(psi),
+                                    ctypes.c_void_p(a_list.data_ptr()), a_list.numel(),
+                                    ctypes.c_void_p(out.data_ptr()), _stream(psi)), "hadamag_sre_terms")
+    return out
+
+
+def mc_xstrings(seed: int, count: int, N: int, device: int = 0) -> torch.Tensor:
+    """SplitMix64 X-strings a_i (top N bits of output i), as drawn by sre_mc."""
+    out = torch.empty(count, dtype=torch.int64, device=f"cuda:{device}")
+    c = context(device)
+    c.check(c.lib.hadamag_mc_xstrings(c.h, ctypes.c_uint64(seed & (2 ** 64 - 1)), count, int(N),
+                                      ctypes.c_void_p(out.data_ptr()), _stream(out)), "hadamag_mc_xstrings")
+    return out
+
+
+def sre_mc(psi: torch.Tensor, samples: int, seed: int):
+    """(M2_hat, stderr) of the uniform-X Monte-Carlo estimator."""
+    N = _check_state(psi)
+    c = _ctx(psi)
+    M, se = ctypes.c_double(), ctypes.c_double()
+    c.check(c.lib.hadamag_sre_mc(c.h, ctypes.c_void_p(psi.data_ptr()), N, int(samples),
+                                 ctypes.c_uint64(seed & (2 ** 64 - 1)), _dtype_code(psi),
+                                 ctypes.byref(M), ctypes.byref(se), _stream(psi)), "hadamag_sre_mc")
+    return M.value, se.value
+
+
+def mana(psi: torch.Tensor):
+    """(mana in bits, sum_u |W(u)|) of an N-qutrit state (Algorithm 5, Eq. mana2)."""
+    N = _check_state(psi, 3)
+    c = _ctx(psi)
+    m, sw = ctypes.c_double(), ctypes.c_double()
+    c.check(c.lib.hadamag_mana(c.h, ctypes.c_void_p(psi.data_ptr()), N, _dtype_code(psi),
+                               ctypes.byref(m), ctypes.byref(sw), _stream(psi)), "hadamag_mana")
+    return m.value, sw.value
+
+
+def mana_sums(psi: torch.Tensor):
+    """[sum |chi|, sum chi, sum chi^2] over all (a, b); W = chi / 3^N."""
+    N = _check_state(psi, 3)
+    c = _ctx(psi)
+    out = (ctypes.c_double * 3)()
+    c.check(c.lib.hadamag_mana_sums(c.h, ctypes.c_void_p(psi.data_ptr()), N, _dtype_code(psi), out,
+                                    _stream(psi)), "hadamag_mana_sums")
+    return list(out)
+
+
+def sre_grad(psi: torch.Tensor):
+    """(M_2, dM_2/dpsi*) -- the Wirtinger gradient on the unnormalised state."""
+    N = _check_state(psi)
+    g = torch.empty_like(psi)
+    c = _ctx(psi)
+    M = ctypes.c_double()
+    c.check(c.lib.hadamag_sre_grad(c.h, ctypes.c_void_p(psi.data_ptr()), N, _dtype_code(psi),
+                                   ctypes.byref(M), ctypes.c_void_p(g.data_ptr()), _stream(psi)),
+            "hadamag_sre_grad")
+    return M.value, g
+
+
+class SREFunction(torch.autograd.Function):
+    """M_2(psi) as a differentiable scalar.  backward returns grad_out * 2 dM_2/dpsi*, which
+    is PyTorch's convention for real functions of complex inputs (grad of |z|^2 is 2z)."""
+
+    @staticmethod
+    def forward(ctx, psi):
+        M2, g = sre_grad(psi.detach().contiguous())
+        ctx.save_for_backward(g)
+        return torch.tensor(M2, dtype=torch.float64, device=psi.device)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        (g,) = ctx.saved_tensors
+        return (2.0 * grad_out.to(g.real.dtype)) * g
+
+
+def sre_batched(states, want_grad: bool = False):
+    """M_2 (and dM_2/dpsi*) of many complex64 states of uneven N in one persistent launch.
+
+    Returns (M2 tensor [count] float64, list of gradients or None)."""
+    if not states:
+        raise ValueError("empty batch")
+    dev = states[0].device
+    Ns, ptrs = [], []
+    for s in states:
+        if s.dtype != torch.complex64 or s.device != dev:
+            raise ValueError("batched states must be complex64 on one device")
+        Ns.append(_check_state(s))
+        ptrs.append(s.data_ptr())
+    grads = [torch.empty_like(s) for s in states] if want_grad else None
+    out = torch.empty(len(states), dtype=torch.float64, device=dev)
+    k = len(states)
+    P = (ctypes.c_void_p * k)(*ptrs)
+    G = (ctypes.c_void_p * k)(*([g.data_ptr() for g in grads] if grads else [0] * k))
+    Narr = (ctypes.c_int * k)(*Ns)
+    c = _ctx(states[0])
+    c.check(c.lib.hadamag_sre_batched(c.h, k, P, Narr, 1 if want_grad else 0, G,
+                                      ctypes.c_void_p(out.data_ptr()), _stream(states[0])),
+            "hadamag_sre_batched")
+    return out, grads

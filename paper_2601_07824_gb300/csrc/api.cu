@@ -1,0 +1,404 @@
+// api.cu -- C ABI of libhadamag (declared in include/hadamag.h): argument checks, context
+// buffers, planning of the launches, result read-back and the final FP64 logarithms.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <cuda_runtime.h>
+
+#include "../../include/hadamag.h"
+#include "ctx.h"
+#include "sre_fwd.h"
+#include "extra.h"
+
+using namespace hm;
+
+extern "C" const char* hadamag_status_string(hadamag_status s) {
+    switch (s) {
+        case HADAMAG_OK: return "ok";
+        case HADAMAG_ERR_INVALID_ARG: return "invalid argument";
+        case HADAMAG_ERR_UNSUPPORTED: return "unsupported";
+        case HADAMAG_ERR_OOM: return "out of memory";
+        case HADAMAG_ERR_CUDA: return "CUDA error";
+        case HADAMAG_ERR_TIMEOUT: return "device wait timed out";
+        case HADAMAG_ERR_NONFINITE: return "non-finite result";
+    }
+    return "unknown status";
+}
+
+namespace hm {
+
+hadamag_status fail(hadamag_ctx_t c, hadamag_status s, const char* fmt, ...) {
+    if (c) {
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(c->last_error, sizeof(c->last_error), fmt, ap);
+        va_end(ap);
+    }
+    return s;
+}
+
+hadamag_status cuda_fail(hadamag_ctx_t c, cudaError_t e, const char* where) {
+    if (e == cudaErrorMemoryAllocation) {
+        cudaGetLastError();
+        return fail(c, HADAMAG_ERR_OOM, "%s: %s", where, cudaGetErrorString(e));
+    }
+    return fail(c, HADAMAG_ERR_CUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+hadamag_status ensure_buf(hadamag_ctx_t c, DevBuf& b, size_t bytes) {
+    if (b.bytes >= bytes && b.ptr) return HADAMAG_OK;
+    if (b.ptr) {
+        cudaError_t e = cudaFree(b.ptr);
+        b.ptr = nullptr;
+        b.bytes = 0;
+        if (e != cudaSuccess) return cuda_fail(c, e, "cudaFree");
+    }
+    size_t sz = bytes < 256 ? 256 : bytes;
+    cudaError_t e = cudaMalloc(&b.ptr, sz);
+    if (e != cudaSuccess) {
+        b.ptr = nullptr;
+        return cuda_fail(c, e, "cudaMalloc");
+    }
+    b.bytes = sz;
+    return HADAMAG_OK;
+}
+
+bool aligned16(const void* p) { return p && ((uintptr_t)p & 15u) == 0; }
+
+// complex128 input -> complex64 copy in the context (the kernels compute in FP32).
+hadamag_status as_c64(hadamag_ctx_t c, const void* psi, int64_t n, hadamag_dtype dt, cudaStream_t st,
+                      const float2** out) {
+    if (dt == HADAMAG_C64) {
+        *out = reinterpret_cast<const float2*>(psi);
+        return HADAMAG_OK;
+    }
+    if (dt != HADAMAG_C128) return fail(c, HADAMAG_ERR_INVALID_ARG, "bad dtype %d", (int)dt);
+    hadamag_status s = ensure_buf(c, c->conv, (size_t)n * sizeof(float2));
+    if (s) return s;
+    cudaError_t e = launch_c128_to_c64(psi, reinterpret_cast<float2*>(c->conv.ptr), n, st);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(c, e, "c128_to_c64");
+    *out = reinterpret_cast<const float2*>(c->conv.ptr);
+    return HADAMAG_OK;
+}
+
+int sre_mode(double n) { return n == 1.0 ? 1 : n == 2.0 ? 2 : n == 3.0 ? 3 : 0; }
+
+TwoPlan plan_twopass(int N) {
+    TwoPlan p{};
+    const int L = N - 1, K1 = twopass_k1(N), M = L - K1;
+    const size_t per_a = ((size_t)1 << L) * sizeof(float2);
+    int A = 1;
+    if (K1 == 10) {
+        A = 8;  // X-strings per batch: pass-1 warps sharing a pair of state rows
+        while (A > 1 && (size_t)A * per_a > ((size_t)16 << 20)) A >>= 1;
+        p.U = 8 / A;
+    } else {
+        p.U = 1;
+    }
+    p.A = A;
+    p.R = (N <= 22) ? 4 : 2;
+    p.tiles = twopass_tiles_per_a(N);
+    // a pass-1 task covers A X-strings x (U or 1) units per warp x 2 units (K1 = 10);
+    // a pass-2 task covers two adjacent column tiles
+    p.p1 = (K1 == 10) ? (1 << M) / (p.U * 2) : (1 << M);
+    p.p2 = A * p.tiles / 2;
+    p.scratch_bytes = (size_t)p.R * A * per_a;
+    return p;
+}
+
+// Runs Algorithm 2 over `count` X-strings (all of them when a_list is null).  per_a = 0:
+// per-CTA partial triples go to c->part and *nparts receives their number.  per_a = 1:
+// per-X-string triples are written to terms (device).
+hadamag_status run_sre(hadamag_ctx_t c, const float2* psi, int N, double n, int64_t count,
+                       const int64_t* a_list, int per_a, double* terms, cudaStream_t st, int64_t* nparts) {
+    const int mode = sre_mode(n);
+    hadamag_status s;
+    cudaError_t e;
+    if (N <= 15) {
+        OnepassArgs A{};
+        A.psi = psi; A.N = N; A.nq = n; A.count = count; A.a_list = a_list;
+        A.per_a = per_a; A.status = (int*)c->status.ptr; A.grid = 0;
+        if (!per_a) {
+            int64_t maxgrid = (int64_t)c->sm_count * 64;
+            if ((s = ensure_buf(c, c->part, (size_t)maxgrid * 3 * sizeof(double)))) return s;
+            A.out = (double*)c->part.ptr;
+            A.grid = (int)maxgrid;
+        } else {
+            A.out = terms;
+        }
+        e = launch_onepass(A, mode, c->sm_count, st);
+        c->launches++;
+        if (e != cudaSuccess) return cuda_fail(c, e, "sre_onepass");
+        if (nparts) *nparts = A.grid;
+        return HADAMAG_OK;
+    }
+    if (N > 24) return fail(c, HADAMAG_ERR_UNSUPPORTED, "exact SRE supports N <= 24 (got %d)", N);
+    TwoPlan pl = plan_twopass(N);
+    int grid = 0;
+    if ((e = twopass_max_grid(N, mode, c->sm_count, &grid)) != cudaSuccess) return cuda_fail(c, e, "occupancy");
+    if ((s = ensure_buf(c, c->scratch, pl.scratch_bytes))) return s;
+    if ((s = ensure_buf(c, c->counters, 2 * 64 * sizeof(unsigned)))) return s;
+    TwoPassParams P{};
+    P.psi = psi; P.N = N; P.nq = n; P.count = count; P.a_list = a_list;
+    P.scratch = (float2*)c->scratch.ptr; P.R = pl.R; P.A = pl.A; P.U = pl.U;
+    P.n_batches = (count + pl.A - 1) / pl.A;
+    P.p1 = pl.p1; P.p2 = pl.p2;
+    P.done1 = (unsigned*)c->counters.ptr; P.done2 = P.done1 + 64;
+    P.status = (int*)c->status.ptr; P.spin_limit = c->spin_limit; P.wait_bias = c->wait_bias;
+    P.per_a = per_a;
+    const int64_t total_tasks = P.n_batches * ((int64_t)pl.p1 + pl.p2);
+    if (grid > total_tasks) grid = (int)total_tasks;
+    if (grid < 1) grid = 1;
+    if (per_a) {
+        if ((s = ensure_buf(c, c->tiles, (size_t)count * pl.tiles * 3 * sizeof(double)))) return s;
+        P.out = (double*)c->tiles.ptr;
+    } else {
+        if ((s = ensure_buf(c, c->part, (size_t)grid * 3 * sizeof(double)))) return s;
+        P.out = (double*)c->part.ptr;
+    }
+    if ((e = cudaMemsetAsync(c->counters.ptr, 0, 2 * 64 * sizeof(unsigned), st)) != cudaSuccess)
+        return cuda_fail(c, e, "memset counters");
+    e = launch_twopass(P, mode, grid, st);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(c, e, "sre_twopass");
+    if (per_a) {
+        e = launch_sum_tiles((double*)c->tiles.ptr, count, pl.tiles, terms, st);
+        c->launches++;
+        if (e != cudaSuccess) return cuda_fail(c, e, "sum_tiles");
+    }
+    if (nparts) *nparts = grid;
+    return HADAMAG_OK;
+}
+
+hadamag_status begin(hadamag_ctx_t c, cudaStream_t st) {
+    c->last_error[0] = 0;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    e = cudaMemsetAsync(c->status.ptr, 0, sizeof(int), st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "memset status");
+    return HADAMAG_OK;
+}
+
+// Copy `n` result doubles and the status word to pinned host memory and wait for the stream.
+hadamag_status finish(hadamag_ctx_t c, const double* res_dev, int n, cudaStream_t st) {
+    cudaError_t e;
+    if (n > 0 && (e = cudaMemcpyAsync(c->host_res, res_dev, n * sizeof(double), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(c, e, "copy result");
+    if ((e = cudaMemcpyAsync(c->host_status, c->status.ptr, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(c, e, "copy status");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "stream sync");
+    return status_word(c);
+}
+
+hadamag_status status_word(hadamag_ctx_t c) {
+    int w = *c->host_status;
+    if (w & ST_TIMEOUT) return fail(c, HADAMAG_ERR_TIMEOUT, "an inter-CTA wait ran out of iterations");
+    if (w & ST_BADARG) return fail(c, HADAMAG_ERR_INVALID_ARG, "an X-string list entry is outside [0, dim)");
+    return HADAMAG_OK;
+}
+
+}  // namespace hm
+
+// ---------------------------------------------------------------------------------------
+extern "C" hadamag_status hadamag_create(hadamag_ctx_t* out, int device) {
+    if (!out) return HADAMAG_ERR_INVALID_ARG;
+    *out = nullptr;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) {
+        cudaGetLastError();
+        return HADAMAG_ERR_INVALID_ARG;
+    }
+    hadamag_ctx_t c = new (std::nothrow) hadamag_ctx_s();
+    if (!c) return HADAMAG_ERR_OOM;
+    c->device = device;
+    cudaError_t e = cudaSetDevice(device);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
+    if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->host_res, 64 * sizeof(double));
+    if (e == cudaSuccess) e = cudaMallocHost((void**)&c->host_status, sizeof(int));
+    if (e != cudaSuccess) {
+        hadamag_destroy(c);
+        cudaGetLastError();
+        return HADAMAG_ERR_CUDA;
+    }
+    if (ensure_buf(c, c->status, sizeof(int)) || ensure_buf(c, c->res, 64 * sizeof(double))) {
+        hadamag_destroy(c);
+        return HADAMAG_ERR_OOM;
+    }
+    *out = c;
+    return HADAMAG_OK;
+}
+
+extern "C" hadamag_status hadamag_destroy(hadamag_ctx_t c) {
+    if (!c) return HADAMAG_OK;
+    cudaSetDevice(c->device);
+    if (c->own_stream) cudaStreamSynchronize(c->own_stream);
+    for (DevBuf* b : c->all_bufs())
+        if (b->ptr) cudaFree(b->ptr);
+    if (c->host_res) cudaFreeHost(c->host_res);
+    if (c->host_status) cudaFreeHost(c->host_status);
+    if (c->own_stream) cudaStreamDestroy(c->own_stream);
+    delete c;
+    return HADAMAG_OK;
+}
+
+extern "C" hadamag_status hadamag_set_path(hadamag_ctx_t c, hadamag_path p) {
+    if (!c || (p != HADAMAG_PATH_AUTO && p != HADAMAG_PATH_CUDACORE && p != HADAMAG_PATH_TENSOR))
+        return HADAMAG_ERR_INVALID_ARG;
+    c->path = p;
+    return HADAMAG_OK;
+}
+
+extern "C" hadamag_status hadamag_set_wait_limit(hadamag_ctx_t c, long long spins, unsigned bias) {
+    if (!c || spins < 1) return HADAMAG_ERR_INVALID_ARG;
+    c->spin_limit = spins;
+    c->wait_bias = bias;
+    return HADAMAG_OK;
+}
+
+extern "C" hadamag_status hadamag_launch_count(hadamag_ctx_t c, uint64_t* n) {
+    if (!c || !n) return HADAMAG_ERR_INVALID_ARG;
+    *n = c->launches;
+    return HADAMAG_OK;
+}
+
+extern "C" const char* hadamag_last_error(hadamag_ctx_t c) { return c ? c->last_error : ""; }
+
+extern "C" hadamag_status hadamag_sre(hadamag_ctx_t c, const void* psi, int N, double n,
+                                      hadamag_dtype dt, double* M_out, double* lost_out,
+                                      hadamag_stream_t stream) {
+    if (!c) return HADAMAG_ERR_INVALID_ARG;
+    if (!aligned16(psi) || !M_out) return fail(c, HADAMAG_ERR_INVALID_ARG, "null or misaligned pointer");
+    if (N < 1 || N > 24) return fail(c, HADAMAG_ERR_INVALID_ARG, "N must be in [1, 24] (got %d)", N);
+    if (!(n > 0.0) || !std::isfinite(n)) return fail(c, HADAMAG_ERR_INVALID_ARG, "n must be > 0");
+    if (dt != HADAMAG_C64 && dt != HADAMAG_C128) return fail(c, HADAMAG_ERR_INVALID_ARG, "bad dtype");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    hadamag_status s;
+    if ((s = begin(c, st))) return s;
+    const int64_t dim = int64_t(1) << N;
+    const float2* p;
+    if ((s = as_c64(c, psi, dim, dt, st, &p))) return s;
+    double sums[3];
+    if ((s = sre_sums(c, p, N, n, st, sums))) return s;
+    return sre_from_sums(c, N, n, sums, M_out, lost_out);
+}
+
+namespace hm {
+
+// Exact per-call sums [S_n, S_1, T_1] over all X-strings, picking the transform path.
+hadamag_status sre_sums(hadamag_ctx_t c, const float2* p, int N, double n, cudaStream_t st, double sums[3]) {
+    hadamag_status s;
+    cudaError_t e;
+    int64_t nparts = 0;
+    const int64_t dim = int64_t(1) << N;
+    bool tensor = use_tensor_path(c, N, n);
+    if (tensor) {
+        if ((s = run_sre_tensor(c, p, N, n, st, &nparts))) return s;
+    } else {
+        if ((s = run_sre(c, p, N, n, dim, nullptr, 0, nullptr, st, &nparts))) return s;
+    }
+    e = launch_sum_triples((const double*)c->part.ptr, nparts, (double*)c->res.ptr, st);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(c, e, "sum_triples");
+    if ((s = finish(c, (const double*)c->res.ptr, 3, st))) return s;
+    sums[0] = c->host_res[0]; sums[1] = c->host_res[1]; sums[2] = c->host_res[2];
+    return HADAMAG_OK;
+}
+
+// Eq. (sre) with the n -> 1 Shannon limit, and lost_norm (Sec. 4.1), in FP64.
+hadamag_status sre_from_sums(hadamag_ctx_t c, int N, double n, const double sums[3], double* M_out,
+                             double* lost_out) {
+    const double two_n = std::ldexp(1.0, N);
+    double M;
+    if (n == 1.0) M = -sums[2] / sums[1] + std::log2(sums[1]) - (double)N;
+    else M = std::log2(sums[0] / two_n) / (1.0 - n);
+    if (M == 0.0) M = 0.0;  // no negative zero
+    *M_out = M;
+    if (lost_out) *lost_out = 1.0 - sums[1] / two_n;
+    if (!std::isfinite(M) || !std::isfinite(sums[1]))
+        return fail(c, HADAMAG_ERR_NONFINITE, "non-finite sums (S_n=%g, S_1=%g)", sums[0], sums[1]);
+    return HADAMAG_OK;
+}
+
+}  // namespace hm
+
+extern "C" hadamag_status hadamag_sre_host(hadamag_ctx_t c, const void* psi_host, int N, double n,
+                                           hadamag_dtype dt, double* M_out, double* lost_out) {
+    if (!c) return HADAMAG_ERR_INVALID_ARG;
+    if (!psi_host || !M_out) return fail(c, HADAMAG_ERR_INVALID_ARG, "null pointer");
+    if (N < 1 || N > 24) return fail(c, HADAMAG_ERR_INVALID_ARG, "N must be in [1, 24] (got %d)", N);
+    if (dt != HADAMAG_C64 && dt != HADAMAG_C128) return fail(c, HADAMAG_ERR_INVALID_ARG, "bad dtype");
+    cudaStream_t st = c->own_stream;
+    hadamag_status s;
+    if ((s = begin(c, st))) return s;
+    const size_t bytes = ((size_t)1 << N) * (dt == HADAMAG_C64 ? 8 : 16);
+    if ((s = ensure_buf(c, c->staging, bytes))) return s;
+    cudaError_t e = cudaMemcpyAsync(c->staging.ptr, psi_host, bytes, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_fail(c, e, "copy psi to device");
+    return hadamag_sre(c, c->staging.ptr, N, n, dt, M_out, lost_out, reinterpret_cast<hadamag_stream_t>(st));
+}
+
+extern "C" hadamag_status hadamag_sre_terms(hadamag_ctx_t c, const void* psi, int N, double n,
+                                            hadamag_dtype dt, const int64_t* a_list, int64_t count,
+                                            double* terms, hadamag_stream_t stream) {
+    if (!c) return HADAMAG_ERR_INVALID_ARG;
+    if (!aligned16(psi) || !a_list || !terms) return fail(c, HADAMAG_ERR_INVALID_ARG, "null or misaligned pointer");
+    if (N < 1 || N > 24) return fail(c, HADAMAG_ERR_INVALID_ARG, "N must be in [1, 24] (got %d)", N);
+    if (!(n > 0.0) || !std::isfinite(n)) return fail(c, HADAMAG_ERR_INVALID_ARG, "n must be > 0");
+    if (count < 0) return fail(c, HADAMAG_ERR_INVALID_ARG, "count < 0");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    hadamag_status s;
+    if ((s = begin(c, st))) return s;
+    if (count == 0) return finish(c, nullptr, 0, st);
+    const float2* p;
+    if ((s = as_c64(c, psi, int64_t(1) << N, dt, st, &p))) return s;
+    if ((s = run_sre(c, p, N, n, count, a_list, 1, terms, st, nullptr))) return s;
+    return finish(c, nullptr, 0, st);
+}
+
+extern "C" hadamag_status hadamag_mc_xstrings(hadamag_ctx_t c, uint64_t seed, int64_t count, int N,
+                                              int64_t* a_out, hadamag_stream_t stream) {
+    if (!c) return HADAMAG_ERR_INVALID_ARG;
+    if (!a_out || count < 0 || N < 1 || N > 30) return fail(c, HADAMAG_ERR_INVALID_ARG, "bad arguments");
+    cudaSetDevice(c->device);
+    if (count == 0) return HADAMAG_OK;
+    cudaError_t e = launch_mc_xstrings(seed, count, N, a_out, reinterpret_cast<cudaStream_t>(stream));
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(c, e, "mc_xstrings");
+    return HADAMAG_OK;
+}
+
+extern "C" hadamag_status hadamag_sre_mc(hadamag_ctx_t c, const void* psi, int N, int64_t samples,
+                                         uint64_t seed, hadamag_dtype dt, double* M2_out,
+                                         double* stderr_out, hadamag_stream_t stream) {
+    if (!c) return HADAMAG_ERR_INVALID_ARG;
+    if (!aligned16(psi) || !M2_out) return fail(c, HADAMAG_ERR_INVALID_ARG, "null or misaligned pointer");
+    if (N < 1 || N > 28) return fail(c, HADAMAG_ERR_INVALID_ARG, "N must be in [1, 28] (got %d)", N);
+    if (samples < 1 || samples > (int64_t(1) << 30)) return fail(c, HADAMAG_ERR_INVALID_ARG, "bad sample count");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    hadamag_status s;
+    if ((s = begin(c, st))) return s;
+    const float2* p;
+    if ((s = as_c64(c, psi, int64_t(1) << N, dt, st, &p))) return s;
+    if ((s = ensure_buf(c, c->alist, (size_t)samples * sizeof(int64_t)))) return s;
+    if ((s = ensure_buf(c, c->terms, (size_t)samples * 3 * sizeof(double)))) return s;
+    int64_t* al = (int64_t*)c->alist.ptr;
+    double* tm = (double*)c->terms.ptr;
+    cudaError_t e = launch_mc_xstrings(seed, samples, N, al, st);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(c, e, "mc_xstrings");
+    if (N <= 24) s = run_sre(c, p, N, 2.0, samples, al, 1, tm, st, nullptr);
+    else s = run_sre_hbm_terms(c, p, N, samples, al, tm, st);
+    if (s) return s;
+    e = launch_mc_stats(tm, samples, (double*)c->res.ptr, st);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(c, e, "mc_stats");
+    if ((s = finish(c, (const double*)c->res.ptr, 2, st))) return s;
+    const double mean = c->host_res[0], var = c->host_res[1];
+    *M2_out = -std::log2(mean);
+    if (stderr_out) *stderr_out = std::sqrt(var / (double)samples) / (mean * std::log(2.0));
+    if (!std::isfinite(*M2_out)) return fail(c, HADAMAG_ERR_NONFINITE, "non-finite estimate");
+    return HADAMAG_OK;
+}

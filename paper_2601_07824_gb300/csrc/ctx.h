@@ -1,0 +1,64 @@
+// ctx.h -- the context object behind hadamag_ctx_t and internal host helpers.
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <initializer_list>
+#include <vector>
+
+#include "../../include/hadamag.h"
+#include "status_bits.h"
+
+namespace hm {
+
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+struct TwoPlan {
+    int A, U, R, p1, p2, tiles;
+    size_t scratch_bytes;
+};
+
+}  // namespace hm
+
+struct hadamag_ctx_s {
+    int device = 0;
+    int sm_count = 0;
+    hadamag_path path = HADAMAG_PATH_AUTO;
+    cudaStream_t own_stream = nullptr;
+    hm::DevBuf status, res, part, scratch, counters, tiles, conv, staging, alist, terms;
+    hm::DevBuf grad_acc, batch_meta, batch_sums, tc_scratch;
+    double* host_res = nullptr;
+    int* host_status = nullptr;
+    long long spin_limit = 1ll << 25;
+    unsigned wait_bias = 0;
+    uint64_t launches = 0;
+    char last_error[256] = {0};
+    std::vector<hm::DevBuf*> all_bufs() {
+        return {&status, &res, &part, &scratch, &counters, &tiles, &conv, &staging, &alist, &terms,
+                &grad_acc, &batch_meta, &batch_sums, &tc_scratch};
+    }
+};
+
+namespace hm {
+
+hadamag_status fail(hadamag_ctx_t c, hadamag_status s, const char* fmt, ...);
+hadamag_status cuda_fail(hadamag_ctx_t c, cudaError_t e, const char* where);
+hadamag_status ensure_buf(hadamag_ctx_t c, DevBuf& b, size_t bytes);
+bool aligned16(const void* p);
+hadamag_status as_c64(hadamag_ctx_t c, const void* psi, int64_t n, hadamag_dtype dt, cudaStream_t st,
+                      const float2** out);
+int sre_mode(double n);
+TwoPlan plan_twopass(int N);
+hadamag_status run_sre(hadamag_ctx_t c, const float2* psi, int N, double n, int64_t count,
+                       const int64_t* a_list, int per_a, double* terms, cudaStream_t st, int64_t* nparts);
+hadamag_status begin(hadamag_ctx_t c, cudaStream_t st);
+hadamag_status finish(hadamag_ctx_t c, const double* res_dev, int n, cudaStream_t st);
+hadamag_status status_word(hadamag_ctx_t c);
+hadamag_status sre_sums(hadamag_ctx_t c, const float2* p, int N, double n, cudaStream_t st, double sums[3]);
+hadamag_status sre_from_sums(hadamag_ctx_t c, int N, double n, const double sums[3], double* M_out,
+                             double* lost_out);
+
+}  // namespace hm

@@ -1,0 +1,21 @@
+// extra.h -- launchers and host paths beyond the exact CUDA-core SRE (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "ctx.h"
+
+namespace hm {
+
+// Monte-Carlo helpers (mc.cu)
+cudaError_t launch_mc_xstrings(uint64_t seed, int64_t count, int N, int64_t* out, cudaStream_t st);
+cudaError_t launch_mc_stats(const double* terms, int64_t count, double* out2, cudaStream_t st);
+hadamag_status run_sre_hbm_terms(hadamag_ctx_t c, const float2* psi, int N, int64_t count,
+                                 const int64_t* a_list, double* terms, cudaStream_t st);
+
+// Tensor-core path (tc.cu)
+bool use_tensor_path(hadamag_ctx_t c, int N, double n);
+hadamag_status run_sre_tensor(hadamag_ctx_t c, const float2* psi, int N, double n, cudaStream_t st,
+                              int64_t* nparts);
+
+}  // namespace hm

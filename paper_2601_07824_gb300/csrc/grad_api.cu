@@ -1,0 +1,96 @@
+// grad_api.cu -- C ABI entry point for dM_2/dpsi* (adjoint kernels in grad.cu).
+#include <cmath>
+
+#include "ctx.h"
+#include "grad.h"
+#include "sre_fwd.h"
+
+using namespace hm;
+
+namespace hm {
+
+// Enqueues the adjoint: gradient written to grad_out (same dtype as `dt`), and the FP64 sums
+// [S_2, S_1, 0] left in c->res (device).  No host synchronisation.
+hadamag_status enqueue_grad(hadamag_ctx_t c, const float2* p, int N, void* grad_out, bool c128, cudaStream_t st) {
+    hadamag_status s;
+    cudaError_t e;
+    const int64_t dim = int64_t(1) << N;
+    int64_t nparts = 0;
+    if (N <= 15) {
+        int groups_max = c->sm_count * 8;
+        const int64_t cap_bytes = (int64_t)512 << 20;  // partial gradients: at most 512 MiB
+        while (groups_max > 1 && (int64_t)groups_max * dim * 8 > cap_bytes) groups_max >>= 1;
+        const int gpc = grad_onepass_gpc(N);
+        if (groups_max < gpc) groups_max = gpc;
+        if ((s = ensure_buf(c, c->grad_acc, (size_t)groups_max * dim * sizeof(float2)))) return s;
+        if ((s = ensure_buf(c, c->part, (size_t)groups_max * 3 * sizeof(double)))) return s;
+        if ((e = cudaMemsetAsync(c->grad_acc.ptr, 0, (size_t)groups_max * dim * sizeof(float2), st)) != cudaSuccess)
+            return cuda_fail(c, e, "memset partials");
+        int ng = 0;
+        e = launch_grad_onepass(p, N, (double*)c->part.ptr, (float2*)c->grad_acc.ptr, groups_max, &ng, st);
+        c->launches++;
+        if (e != cudaSuccess) return cuda_fail(c, e, "grad_onepass");
+        nparts = ng;
+    } else {
+        GradParams P{};
+        const int M = N - 11;
+        const size_t per_a = (size_t)dim / 2 * sizeof(float2);
+        int A = 8;
+        while (A > 1 && (size_t)A * per_a > ((size_t)16 << 20)) A >>= 1;
+        P.psi = p; P.N = N; P.R = 3; P.A = A; P.U = 8 / A;
+        P.n_batches = dim / A;
+        P.p1 = (1 << M) / (P.U * 2);
+        P.p2 = A * (1024 >> (13 - M));
+        P.p3 = A * ((1 << M) / 16);
+        int grid = 0;
+        if ((e = grad_threepass_grid(N, c->sm_count, &grid)) != cudaSuccess) return cuda_fail(c, e, "occupancy");
+        if ((s = ensure_buf(c, c->scratch, (size_t)P.R * A * per_a))) return s;
+        if ((s = ensure_buf(c, c->counters, 3 * 64 * sizeof(unsigned)))) return s;
+        if ((s = ensure_buf(c, c->grad_acc, (size_t)grid * dim * sizeof(float2)))) return s;
+        if ((s = ensure_buf(c, c->part, (size_t)grid * 3 * sizeof(double)))) return s;
+        if ((e = cudaMemsetAsync(c->grad_acc.ptr, 0, (size_t)grid * dim * sizeof(float2), st)) != cudaSuccess)
+            return cuda_fail(c, e, "memset partials");
+        if ((e = cudaMemsetAsync(c->counters.ptr, 0, 3 * 64 * sizeof(unsigned), st)) != cudaSuccess)
+            return cuda_fail(c, e, "memset counters");
+        P.scratch = (float2*)c->scratch.ptr;
+        P.done1 = (unsigned*)c->counters.ptr; P.done2 = P.done1 + 64; P.done3 = P.done1 + 128;
+        P.status = (int*)c->status.ptr; P.spin_limit = c->spin_limit; P.wait_bias = c->wait_bias;
+        P.gpart = (float2*)c->grad_acc.ptr;
+        P.sums = (double*)c->part.ptr;
+        e = launch_grad_threepass(P, grid, st);
+        c->launches++;
+        if (e != cudaSuccess) return cuda_fail(c, e, "grad_threepass");
+        nparts = grid;
+    }
+    e = launch_sum_triples((const double*)c->part.ptr, nparts, (double*)c->res.ptr, st);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(c, e, "sum_triples");
+    e = launch_grad_finalize((const float2*)c->grad_acc.ptr, nparts, dim, (const double*)c->res.ptr, grad_out, c128, st);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(c, e, "grad_finalize");
+    return HADAMAG_OK;
+}
+
+}  // namespace hm
+
+extern "C" hadamag_status hadamag_sre_grad(hadamag_ctx_t c, const void* psi, int N, hadamag_dtype dt,
+                                           double* M2_out, void* grad, hadamag_stream_t stream) {
+    if (!c) return HADAMAG_ERR_INVALID_ARG;
+    if (!aligned16(psi) || !aligned16(grad) || !M2_out)
+        return fail(c, HADAMAG_ERR_INVALID_ARG, "null or misaligned pointer");
+    if (N < 1 || N > 20) return fail(c, HADAMAG_ERR_INVALID_ARG, "gradient needs 1 <= N <= 20 (got %d)", N);
+    if (dt != HADAMAG_C64 && dt != HADAMAG_C128) return fail(c, HADAMAG_ERR_INVALID_ARG, "bad dtype");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    hadamag_status s;
+    if ((s = begin(c, st))) return s;
+    const float2* p;
+    if ((s = as_c64(c, psi, int64_t(1) << N, dt, st, &p))) return s;
+    if ((s = enqueue_grad(c, p, N, grad, dt == HADAMAG_C128, st))) return s;
+    if ((s = finish(c, (const double*)c->res.ptr, 3, st))) return s;
+    const double S2 = c->host_res[0];
+    double M2 = -std::log2(S2 / std::ldexp(1.0, N));
+    if (M2 == 0.0) M2 = 0.0;
+    *M2_out = M2;
+    if (!std::isfinite(M2)) return fail(c, HADAMAG_ERR_NONFINITE, "non-finite S_2");
+    return HADAMAG_OK;
+}

@@ -1,0 +1,102 @@
+// mana_api.cu -- C ABI entry points for the qutrit mana (Algorithm 5, Eq. mana2).
+#include <cmath>
+
+#include "ctx.h"
+#include "mana.h"
+#include "sre_fwd.h"
+
+using namespace hm;
+
+namespace {
+
+int64_t ipow3(int n) {
+    int64_t r = 1;
+    while (n-- > 0) r *= 3;
+    return r;
+}
+
+// sums = [sum_{a,b} |chi_b(a)|, sum chi_b(a), sum chi_b(a)^2] (device FP64, then host).
+hadamag_status mana_sums(hadamag_ctx_t c, const void* psi, int N, hadamag_dtype dt, cudaStream_t st,
+                         double sums[3]) {
+    hadamag_status s;
+    cudaError_t e;
+    if ((s = begin(c, st))) return s;
+    const int64_t dim = ipow3(N);
+    const float2* p;
+    if ((s = as_c64(c, psi, dim, dt, st, &p))) return s;
+    int64_t nparts = 0;
+    if (N <= 8) {
+        if ((s = ensure_buf(c, c->part, (size_t)c->sm_count * 64 * 3 * sizeof(double)))) return s;
+        int grid = 0;
+        e = launch_mana_onepass(p, N, (double*)c->part.ptr, c->sm_count, &grid, st);
+        c->launches++;
+        if (e != cudaSuccess) return cuda_fail(c, e, "mana_onepass");
+        nparts = grid;
+    } else {
+        const int M = N - 8;
+        const size_t per_a = (size_t)dim * sizeof(float2);
+        int A = 8;
+        while (A > 1 && (size_t)A * per_a > ((size_t)16 << 20)) A >>= 1;
+        ManaParams P{};
+        P.psi = p; P.N = N; P.count = dim; P.R = 3; P.A = A;
+        P.n_batches = (dim + A - 1) / A;
+        P.p1 = P.p2 = A * (int)ipow3(M);
+        int grid = 0;
+        if ((e = mana_twopass_grid(N, c->sm_count, &grid)) != cudaSuccess) return cuda_fail(c, e, "occupancy");
+        const int64_t total = P.n_batches * ((int64_t)P.p1 + P.p2);
+        if (grid > total) grid = (int)total;
+        if ((s = ensure_buf(c, c->scratch, (size_t)P.R * A * per_a))) return s;
+        if ((s = ensure_buf(c, c->counters, 2 * 64 * sizeof(unsigned)))) return s;
+        if ((s = ensure_buf(c, c->part, (size_t)grid * 3 * sizeof(double)))) return s;
+        P.scratch = (float2*)c->scratch.ptr;
+        P.done1 = (unsigned*)c->counters.ptr; P.done2 = P.done1 + 64;
+        P.status = (int*)c->status.ptr; P.spin_limit = c->spin_limit; P.wait_bias = c->wait_bias;
+        P.out = (double*)c->part.ptr;
+        if ((e = cudaMemsetAsync(c->counters.ptr, 0, 2 * 64 * sizeof(unsigned), st)) != cudaSuccess)
+            return cuda_fail(c, e, "memset counters");
+        e = launch_mana_twopass(P, grid, st);
+        c->launches++;
+        if (e != cudaSuccess) return cuda_fail(c, e, "mana_twopass");
+        nparts = grid;
+    }
+    e = launch_sum_triples((const double*)c->part.ptr, nparts, (double*)c->res.ptr, st);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(c, e, "sum_triples");
+    if ((s = finish(c, (const double*)c->res.ptr, 3, st))) return s;
+    sums[0] = c->host_res[0]; sums[1] = c->host_res[1]; sums[2] = c->host_res[2];
+    return HADAMAG_OK;
+}
+
+hadamag_status check_args(hadamag_ctx_t c, const void* psi, int N, hadamag_dtype dt) {
+    if (!aligned16(psi)) return fail(c, HADAMAG_ERR_INVALID_ARG, "null or misaligned pointer");
+    if (N < 1 || N > 13) return fail(c, HADAMAG_ERR_INVALID_ARG, "mana needs 1 <= N <= 13 (got %d)", N);
+    if (dt != HADAMAG_C64 && dt != HADAMAG_C128) return fail(c, HADAMAG_ERR_INVALID_ARG, "bad dtype");
+    return HADAMAG_OK;
+}
+
+}  // namespace
+
+extern "C" hadamag_status hadamag_mana(hadamag_ctx_t c, const void* psi, int N, hadamag_dtype dt,
+                                       double* mana_out, double* sum_w_out, hadamag_stream_t stream) {
+    if (!c) return HADAMAG_ERR_INVALID_ARG;
+    hadamag_status s;
+    if ((s = check_args(c, psi, N, dt))) return s;
+    double sums[3];
+    if ((s = mana_sums(c, psi, N, dt, reinterpret_cast<cudaStream_t>(stream), sums))) return s;
+    const double sw = sums[0] / (double)ipow3(N);  // Eq. (mana2): sum_u |W(u)| = m / 3^N
+    double m = std::log2(sw);
+    if (m == 0.0) m = 0.0;
+    if (mana_out) *mana_out = m;
+    if (sum_w_out) *sum_w_out = sw;
+    if (!std::isfinite(m)) return fail(c, HADAMAG_ERR_NONFINITE, "non-finite mana");
+    return HADAMAG_OK;
+}
+
+extern "C" hadamag_status hadamag_mana_sums(hadamag_ctx_t c, const void* psi, int N, hadamag_dtype dt,
+                                            double* sums_out, hadamag_stream_t stream) {
+    if (!c) return HADAMAG_ERR_INVALID_ARG;
+    if (!sums_out) return fail(c, HADAMAG_ERR_INVALID_ARG, "null output");
+    hadamag_status s;
+    if ((s = check_args(c, psi, N, dt))) return s;
+    return mana_sums(c, psi, N, dt, reinterpret_cast<cudaStream_t>(stream), sums_out);
+}

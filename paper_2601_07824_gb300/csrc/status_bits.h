@@ -1,0 +1,5 @@
+// status_bits.h -- bits a kernel may set in the context's device status word.
+#pragma once
+namespace hm {
+enum : int { ST_TIMEOUT = 1, ST_BADARG = 2 };
+}
