@@ -159,6 +159,26 @@ hadamag_status hadamag_sre_batched(hadamag_ctx_t ctx, int count, const void* con
                                    const int* N, int want_grad, void* const* grad_dev,
                                    double* M2_dev, hadamag_stream_t stream);
 
+/*
+ * Allocation-free exact SRE (the paper has no counterpart; this is a calling convenience).
+ * For callers that cannot allocate device memory where they need the number: work enqueued
+ * during a stream capture in the global capture mode, code whose device memory is entirely
+ * owned by a framework pool or fixed budget, and loops that must not pay the device
+ * synchronisation of cudaMalloc/cudaFree.  No context is needed and nothing is allocated:
+ * the scratch is a fixed 8.06 MiB __device__ array inside the library, held by every GPU
+ * that loads the library until the process exits.
+ *   psi_dev: 2^N complex64 amplitudes on the current device, 16-byte aligned.
+ *   16 <= N <= 20 (other N: HADAMAG_ERR_UNSUPPORTED, nothing enqueued); n > 0 as hadamag_sre.
+ *   out_dev: 3 doubles on the device, written in stream order: [M_n, lost_norm, status]
+ *   (status 0 = ok; otherwise the device-side check bits, and M_n is NaN).
+ * The call enqueues its kernels on `stream` and returns without synchronising.  Every call
+ * on a device shares the same array (it keeps the last call's contents; each call clears
+ * what must start at zero), so calls that overlap on the GPU race: serialise them.  The
+ * first call on a device looks up the array's address; make it before any stream capture.
+ */
+hadamag_status hadamag_sre_noalloc(const void* psi_dev, int N, double n, double* out_dev,
+                                   hadamag_stream_t stream);
+
 #ifdef __cplusplus
 }
 #endif
