@@ -92,7 +92,9 @@ hadamag_status hadamag_sre_host(hadamag_ctx_t ctx, const void* psi_host, int N, 
  * Per-X-string sums of Algorithm 2 for an explicit list of X-strings:
  *     terms_dev[3i+0] = sum_b |chi_b(a_i)|^{2n},  terms_dev[3i+1] = sum_b |chi_b(a_i)|^2,
  *     terms_dev[3i+2] = sum_b |chi_b|^2 log2 |chi_b|^2 (n = 1 only, else 0),
- * with chi_b(a) = <psi| X_a Z_b |psi> (Eq. Z_FT_qubits).  a_list_dev: `count` int64 entries
+ * with chi_b(a) = <psi| X_a Z_b |psi> (Eq. Z_FT_qubits).  1 <= N <= 28 (n = 2 only for N > 24,
+ * where the scratch of one X-string exceeds L2 and a three-pass HBM schedule is used).
+ * a_list_dev: `count` int64 entries
  * in [0, 2^N) on the device (an entry outside gives INVALID_ARG after the launch and its
  * terms are left unwritten).  terms_dev: count*3 doubles on the device.  Stream-ordered;
  * synchronises `stream` to read the status word.
@@ -110,11 +112,14 @@ hadamag_status hadamag_mc_xstrings(hadamag_ctx_t ctx, uint64_t seed, int64_t cou
                                    int64_t* a_out_dev, hadamag_stream_t stream);
 
 /*
- * Uniform-X Monte-Carlo M_2: S_hat = mean_i sum_b |chi_b(a_i)|^4 over `samples` X-strings
- * drawn as in hadamag_mc_xstrings; M2_hat = -log2(S_hat) (an unbiased estimate of
- * S_2 / 2^N, from the per-X decomposition of Algorithm 2); stderr_out = sd / (sqrt(samples)
- * S_hat ln 2) (Eq. M2mNcerror).  1 <= N <= 28 (N >= 25 uses a two-pass HBM schedule).
- * stderr_out may be NULL.  Synchronises `stream`.
+ * Uniform-X Monte-Carlo M_2 (from the per-X decomposition of Algorithm 2): with
+ * S(a) = sum_b |chi_b(a)|^4, the X-string a = 0 (it holds the identity string, which the paper
+ * also takes out of its sampling, Sec. 4.2 footnote) is evaluated exactly and `samples`
+ * X-strings are drawn as in hadamag_mc_xstrings, those equal to 0 being dropped:
+ *     S_hat = [S(0) + (2^N - 1) mean_{a_i != 0} S(a_i)] / 2^N  (unbiased for S_2 / 2^N),
+ *     M2_hat = -log2(S_hat),  stderr = (1 - 2^-N) sd / sqrt(n) / (S_hat ln 2) (Eq. M2mNcerror).
+ * 1 <= N <= 28 (N >= 25 uses a three-pass HBM schedule).  stderr_out may be NULL.
+ * Synchronises `stream`.
  */
 hadamag_status hadamag_sre_mc(hadamag_ctx_t ctx, const void* psi_dev, int N, int64_t samples,
                               uint64_t seed, hadamag_dtype dtype, double* M2_out,
@@ -148,16 +153,23 @@ hadamag_status hadamag_sre_grad(hadamag_ctx_t ctx, const void* psi_dev, int N, h
                                 double* M2_out, void* grad_dev, hadamag_stream_t stream);
 
 /*
- * Many states of uneven N (1 <= N_i <= 18) in one persistent launch: M_2 of each into
- * M2_dev[i] (device doubles) and, if want_grad, dM_2/dpsi* into grad_dev[i].  psi_dev and
- * grad_dev are HOST arrays of `count` device pointers (complex64 only).  Work is split into
- * (state, X-string chunk) items scheduled largest first; chunk sizes come from the
- * context's autotuner.  Stream-ordered; no host sync, so it can be captured in a CUDA graph
- * after one uncaptured warm-up call with the same shapes.
+ * Many states of uneven N (10 <= N_i <= 18, complex64) in ONE persistent launch (the batched
+ * form of configs[3]; not in the paper): M_2 of state i into M2_dev[i] (device doubles) and, if
+ * want_grad, dM_2/dpsi* into grad_dev[i] (complex64).  psi_dev and grad_dev are HOST arrays of
+ * `count` device pointers.  States with N <= 14 are one CTA item each; larger states run the
+ * three-pass adjoint; the work list is ordered largest first and taken through a dynamic
+ * ticket counter.  The X-strings per pass-1 task come from the context's autotuner (timed on
+ * the first uncaptured call for a given set of sizes).  Stream-ordered, no host sync and no
+ * allocation once the context's buffers have grown, so after one uncaptured call with the same
+ * shapes the call can be captured in a CUDA graph.  Read the device status with
+ * hadamag_batched_status.
  */
 hadamag_status hadamag_sre_batched(hadamag_ctx_t ctx, int count, const void* const* psi_dev,
                                    const int* N, int want_grad, void* const* grad_dev,
                                    double* M2_dev, hadamag_stream_t stream);
+/* Synchronises `stream` and reports the device status word of the preceding batched call
+ * (HADAMAG_OK, or HADAMAG_ERR_TIMEOUT if a bounded wait ran out). */
+hadamag_status hadamag_batched_status(hadamag_ctx_t ctx, hadamag_stream_t stream);
 
 /*
  * Allocation-free exact SRE (the paper has no counterpart; this is a calling convenience).

@@ -30,8 +30,11 @@
  *       dM2/dpsi*_w = -1/(ln2 S_2) sum_a psi_{w xor a} [G_a(w) + conj(G_a(w xor a))],
  *       G_a = H^{(x)N}(2 |c_a|^2 c_a), c_a = H^{(x)N} v_a.
  *   R6  Uniform-X Monte Carlo (not an algorithm of the paper; it follows from the per-X
- *       decomposition of Algorithm 2): a_i = top N bits of SplitMix64 output i,
- *       S_hat = mean_i S(a_i) with S(a) = sum_b |chi_b(a)|^4, M2_hat = -log2(S_hat).
+ *       decomposition of Algorithm 2): a_i = top N bits of SplitMix64 output i, S(a) =
+ *       sum_b |chi_b(a)|^4.  As the paper does for the identity string (Sec. 4.2 footnote: it is
+ *       excluded from sampling and its contribution added exactly), the X-string a = 0, which
+ *       contains the identity, is evaluated exactly and the samples with a_i = 0 are dropped:
+ *       S_hat = [S(0) + (2^N - 1) mean_{a_i != 0} S(a_i)] / 2^N, M2_hat = -log2(S_hat).
  *
  * All state vectors are interleaved (re, im) doubles.  Functions return 0 on success and
  * a negative number on bad arguments or allocation failure.
@@ -271,15 +274,23 @@ int orc_sre_mc(const double *psi_ri, int N, int64_t samples, uint64_t seed, int 
     }
     orc_mc_xstrings(seed, samples, N, a);
     int rc = orc_sre_terms_list(psi_ri, N, a, samples, nthreads, S);
+    double S0 = 0.0;
+    int64_t zero = 0;
+    if (rc == 0) rc = orc_sre_terms_list(psi_ri, N, &zero, 1, nthreads, &S0);
     if (rc == 0) {
         double mean = 0.0, var = 0.0;
-        for (int64_t i = 0; i < samples; ++i) mean += S[i];
-        mean /= (double)samples;
-        for (int64_t i = 0; i < samples; ++i) var += (S[i] - mean) * (S[i] - mean);
-        var = samples > 1 ? var / (double)(samples - 1) : 0.0;
-        *M2_hat = -log2(mean);
-        /* delta M ~ (1/ln 2) delta S / S with delta S = sd / sqrt(n) (Eq. M2mNcerror) */
-        *stderr_out = sqrt(var / (double)samples) / (mean * log(2.0));
+        int64_t n = 0;
+        for (int64_t i = 0; i < samples; ++i)
+            if (a[i] != 0) { mean += S[i]; ++n; }
+        mean = n ? mean / (double)n : 0.0;
+        for (int64_t i = 0; i < samples; ++i)
+            if (a[i] != 0) var += (S[i] - mean) * (S[i] - mean);
+        var = n > 1 ? var / (double)(n - 1) : 0.0;
+        const double two_n = ldexp(1.0, N), w = (two_n - 1.0) / two_n;
+        const double Shat = S0 / two_n + w * mean;
+        *M2_hat = -log2(Shat);
+        /* delta M ~ (1/ln 2) delta S / S with delta S = w sd / sqrt(n) (Eq. M2mNcerror) */
+        *stderr_out = n ? w * sqrt(var / (double)n) / (Shat * log(2.0)) : 0.0;
     }
     free(a);
     if (!S_per_sample) free(S);

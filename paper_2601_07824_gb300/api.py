@@ -158,10 +158,12 @@ class SREFunction(torch.autograd.Function):
         return (2.0 * grad_out.to(g.real.dtype)) * g
 
 
-def sre_batched(states, want_grad: bool = False):
-    """M_2 (and dM_2/dpsi*) of many complex64 states of uneven N in one persistent launch.
+def sre_batched(states, want_grad: bool = False, out=None, grads=None, sync: bool = True):
+    """M_2 (and dM_2/dpsi*) of many complex64 states of uneven N (10..18) in one persistent launch.
 
-    Returns (M2 tensor [count] float64, list of gradients or None)."""
+    Returns (M2 tensor [count] float64, list of gradients or None).  With sync=False nothing
+    waits on the host (the call can be captured in a CUDA graph after one uncaptured call with
+    the same shapes); pass preallocated `out` / `grads` then."""
     if not states:
         raise ValueError("empty batch")
     dev = states[0].device
@@ -171,14 +173,18 @@ def sre_batched(states, want_grad: bool = False):
             raise ValueError("batched states must be complex64 on one device")
         Ns.append(_check_state(s))
         ptrs.append(s.data_ptr())
-    grads = [torch.empty_like(s) for s in states] if want_grad else None
-    out = torch.empty(len(states), dtype=torch.float64, device=dev)
+    if want_grad and grads is None:
+        grads = [torch.empty_like(s) for s in states]
+    if out is None:
+        out = torch.empty(len(states), dtype=torch.float64, device=dev)
     k = len(states)
     P = (ctypes.c_void_p * k)(*ptrs)
-    G = (ctypes.c_void_p * k)(*([g.data_ptr() for g in grads] if grads else [0] * k))
+    G = (ctypes.c_void_p * k)(*([g.data_ptr() for g in grads] if want_grad else [0] * k))
     Narr = (ctypes.c_int * k)(*Ns)
     c = _ctx(states[0])
     c.check(c.lib.hadamag_sre_batched(c.h, k, P, Narr, 1 if want_grad else 0, G,
                                       ctypes.c_void_p(out.data_ptr()), _stream(states[0])),
             "hadamag_sre_batched")
-    return out, grads
+    if sync:
+        c.check(c.lib.hadamag_batched_status(c.h, _stream(states[0])), "hadamag_batched_status")
+    return out, (grads if want_grad else None)

@@ -3,6 +3,7 @@
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <cuda_runtime.h>
 
@@ -108,6 +109,50 @@ TwoPlan plan_twopass(int N) {
     return p;
 }
 
+// Warp-specialised kernel for 16 <= N <= 20 (one CTA per SM).
+hadamag_status run_sre_ws(hadamag_ctx_t c, const float2* psi, int N, double n, int64_t count,
+                          const int64_t* a_list, int per_a, double* terms, cudaStream_t st, int64_t* nparts) {
+    hadamag_status s;
+    cudaError_t e;
+    const int L = N - 1, M = N - 11;
+    const size_t per_x = ((size_t)1 << L) * sizeof(float2);
+    int A = 8;
+    while (A > 1 && (size_t)A * per_x > ((size_t)16 << 20)) A >>= 1;
+    WsParams P{};
+    P.psi = psi; P.N = N; P.nq = n; P.count = count; P.a_list = a_list;
+    P.R = 4; P.A = A;
+    P.n_batches = (count + A - 1) / A;
+    P.p1 = A * (1 << M) / 2;
+    const int tiles = ws_tiles_per_a(N);
+    P.p2 = A * tiles;
+    int grid = c->sm_count;
+    if ((s = ensure_buf(c, c->scratch, (size_t)P.R * A * per_x))) return s;
+    if ((s = ensure_buf(c, c->counters, 2 * 64 * sizeof(unsigned)))) return s;
+    P.scratch = (float2*)c->scratch.ptr;
+    P.done1 = (unsigned*)c->counters.ptr; P.done2 = P.done1 + 64;
+    P.status = (int*)c->status.ptr; P.spin_limit = c->spin_limit; P.wait_bias = c->wait_bias;
+    P.per_a = per_a;
+    if (per_a) {
+        if ((s = ensure_buf(c, c->tiles, (size_t)count * tiles * 3 * sizeof(double)))) return s;
+        P.out = (double*)c->tiles.ptr;
+    } else {
+        if ((s = ensure_buf(c, c->part, (size_t)grid * 3 * sizeof(double)))) return s;
+        P.out = (double*)c->part.ptr;
+    }
+    if ((e = cudaMemsetAsync(c->counters.ptr, 0, 2 * 64 * sizeof(unsigned), st)) != cudaSuccess)
+        return cuda_fail(c, e, "memset counters");
+    e = launch_ws(P, sre_mode(n), grid, st);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(c, e, "sre_ws");
+    if (per_a) {
+        e = launch_sum_tiles((double*)c->tiles.ptr, count, tiles, terms, st);
+        c->launches++;
+        if (e != cudaSuccess) return cuda_fail(c, e, "sum_tiles");
+    }
+    if (nparts) *nparts = grid;
+    return HADAMAG_OK;
+}
+
 // Runs Algorithm 2 over `count` X-strings (all of them when a_list is null).  per_a = 0:
 // per-CTA partial triples go to c->part and *nparts receives their number.  per_a = 1:
 // per-X-string triples are written to terms (device).
@@ -135,6 +180,7 @@ hadamag_status run_sre(hadamag_ctx_t c, const float2* psi, int N, double n, int6
         return HADAMAG_OK;
     }
     if (N > 24) return fail(c, HADAMAG_ERR_UNSUPPORTED, "exact SRE supports N <= 24 (got %d)", N);
+    if (N <= 20 && c->sre_kernel == 1) return run_sre_ws(c, psi, N, n, count, a_list, per_a, terms, st, nparts);
     TwoPlan pl = plan_twopass(N);
     int grid = 0;
     if ((e = twopass_max_grid(N, mode, c->sm_count, &grid)) != cudaSuccess) return cuda_fail(c, e, "occupancy");
@@ -213,6 +259,7 @@ extern "C" hadamag_status hadamag_create(hadamag_ctx_t* out, int device) {
     hadamag_ctx_t c = new (std::nothrow) hadamag_ctx_s();
     if (!c) return HADAMAG_ERR_OOM;
     c->device = device;
+    if (const char* k = getenv("HADAMAG_SRE_KERNEL")) c->sre_kernel = (strcmp(k, "ws") == 0) ? 1 : 0;
     cudaError_t e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);
@@ -238,6 +285,7 @@ extern "C" hadamag_status hadamag_destroy(hadamag_ctx_t c) {
     for (DevBuf* b : c->all_bufs())
         if (b->ptr) cudaFree(b->ptr);
     if (c->host_res) cudaFreeHost(c->host_res);
+    if (c->host_table) cudaFreeHost(c->host_table);
     if (c->host_status) cudaFreeHost(c->host_status);
     if (c->own_stream) cudaStreamDestroy(c->own_stream);
     delete c;
@@ -345,8 +393,9 @@ extern "C" hadamag_status hadamag_sre_terms(hadamag_ctx_t c, const void* psi, in
                                             double* terms, hadamag_stream_t stream) {
     if (!c) return HADAMAG_ERR_INVALID_ARG;
     if (!aligned16(psi) || !a_list || !terms) return fail(c, HADAMAG_ERR_INVALID_ARG, "null or misaligned pointer");
-    if (N < 1 || N > 24) return fail(c, HADAMAG_ERR_INVALID_ARG, "N must be in [1, 24] (got %d)", N);
+    if (N < 1 || N > 28) return fail(c, HADAMAG_ERR_INVALID_ARG, "N must be in [1, 28] (got %d)", N);
     if (!(n > 0.0) || !std::isfinite(n)) return fail(c, HADAMAG_ERR_INVALID_ARG, "n must be > 0");
+    if (N > 24 && n != 2.0) return fail(c, HADAMAG_ERR_UNSUPPORTED, "N > 24 supports n = 2 only");
     if (count < 0) return fail(c, HADAMAG_ERR_INVALID_ARG, "count < 0");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     hadamag_status s;
@@ -354,7 +403,9 @@ extern "C" hadamag_status hadamag_sre_terms(hadamag_ctx_t c, const void* psi, in
     if (count == 0) return finish(c, nullptr, 0, st);
     const float2* p;
     if ((s = as_c64(c, psi, int64_t(1) << N, dt, st, &p))) return s;
-    if ((s = run_sre(c, p, N, n, count, a_list, 1, terms, st, nullptr))) return s;
+    if (N <= 24) s = run_sre(c, p, N, n, count, a_list, 1, terms, st, nullptr);
+    else s = run_sre_hbm_terms(c, p, N, count, a_list, terms, st);
+    if (s) return s;
     return finish(c, nullptr, 0, st);
 }
 
@@ -382,23 +433,27 @@ extern "C" hadamag_status hadamag_sre_mc(hadamag_ctx_t c, const void* psi, int N
     if ((s = begin(c, st))) return s;
     const float2* p;
     if ((s = as_c64(c, psi, int64_t(1) << N, dt, st, &p))) return s;
-    if ((s = ensure_buf(c, c->alist, (size_t)samples * sizeof(int64_t)))) return s;
-    if ((s = ensure_buf(c, c->terms, (size_t)samples * 3 * sizeof(double)))) return s;
+    // samples, then the exactly evaluated X-string a = 0 (the row holding the identity string)
+    if ((s = ensure_buf(c, c->alist, (size_t)(samples + 1) * sizeof(int64_t)))) return s;
+    if ((s = ensure_buf(c, c->terms, (size_t)(samples + 1) * 3 * sizeof(double)))) return s;
     int64_t* al = (int64_t*)c->alist.ptr;
     double* tm = (double*)c->terms.ptr;
     cudaError_t e = launch_mc_xstrings(seed, samples, N, al, st);
     c->launches++;
     if (e != cudaSuccess) return cuda_fail(c, e, "mc_xstrings");
-    if (N <= 24) s = run_sre(c, p, N, 2.0, samples, al, 1, tm, st, nullptr);
-    else s = run_sre_hbm_terms(c, p, N, samples, al, tm, st);
+    if ((e = cudaMemsetAsync(al + samples, 0, sizeof(int64_t), st)) != cudaSuccess) return cuda_fail(c, e, "memset");
+    if (N <= 24) s = run_sre(c, p, N, 2.0, samples + 1, al, 1, tm, st, nullptr);
+    else s = run_sre_hbm_terms(c, p, N, samples + 1, al, tm, st);
     if (s) return s;
-    e = launch_mc_stats(tm, samples, (double*)c->res.ptr, st);
+    e = launch_mc_stats(tm, al, samples, (double*)c->res.ptr, st);
     c->launches++;
     if (e != cudaSuccess) return cuda_fail(c, e, "mc_stats");
-    if ((s = finish(c, (const double*)c->res.ptr, 2, st))) return s;
-    const double mean = c->host_res[0], var = c->host_res[1];
-    *M2_out = -std::log2(mean);
-    if (stderr_out) *stderr_out = std::sqrt(var / (double)samples) / (mean * std::log(2.0));
+    if ((s = finish(c, (const double*)c->res.ptr, 4, st))) return s;
+    const double mean = c->host_res[0], var = c->host_res[1], n_nz = c->host_res[2], S0 = c->host_res[3];
+    const double two_n = std::ldexp(1.0, N), w = (two_n - 1.0) / two_n;
+    const double Shat = S0 / two_n + w * mean;
+    *M2_out = -std::log2(Shat);
+    if (stderr_out) *stderr_out = n_nz > 0.0 ? w * std::sqrt(var / n_nz) / (Shat * std::log(2.0)) : 0.0;
     if (!std::isfinite(*M2_out)) return fail(c, HADAMAG_ERR_NONFINITE, "non-finite estimate");
     return HADAMAG_OK;
 }

@@ -1,0 +1,157 @@
+// batched.cu -- M_2 and dM_2/dpsi* of many states of uneven N in ONE persistent launch.
+//
+// Work list (built on the host, largest first), taken through a dynamic ticket counter:
+//   * small states (N <= 14): one self-contained item per state, done by one CTA: every X-string
+//     with the one-pass adjoint (grad_phases.cuh), a private partial gradient per thread group,
+//     then the CTA reduces the partials in a fixed order and writes dM_2/dpsi* and M_2;
+//   * large states (15 <= N <= 18): the three passes of the adjoint (pass 1/2/3 tasks in stage
+//     order, runtime dispatch on M = N - 11), scattering into per-CTA partial gradients shared by
+//     all large states, followed by finalize tasks that reduce those partials (FP64, fixed CTA
+//     order), write the gradient, zero the partials and release them to the next large state.
+// Every wait is on a task with a smaller ticket, which a running CTA already holds, so the
+// launch cannot deadlock (waits are bounded and report a timeout through the status word).
+// Assignment of tasks to CTAs is dynamic, so sums may differ between runs in the last bits.
+#include "batched.h"
+#include "grad_phases.cuh"
+
+namespace hm {
+
+template <int L>
+__device__ __forceinline__ void small_item(const BatchState& s, float2* smem, double* m2_out, int idx) {
+    constexpr int G = OnepassShape<L>::G, GPC = 256 / G;  // groups of one 256-thread CTA
+    static_assert(L >= 9 && L <= 13, "small items cover N = 10..14");
+    __shared__ double sums[GPC][2];
+    const uint32_t tid = threadIdx.x, gi = tid / G, t = tid % G;
+    const int64_t dim = int64_t(1) << L << 1;
+    float2* sm = smem + (size_t)gi * tile_slots(L);
+    double acc = 0.0, acc1 = 0.0;
+    grad_onepass_group<L>(s.psi, L + 1, s.gsmall + (size_t)gi * dim, gi, GPC, sm, acc, acc1);
+    if (t == 0) { sums[gi][0] = acc; sums[gi][1] = acc1; }
+    __syncthreads();
+    double S2 = 0.0;
+    for (int k = 0; k < GPC; ++k) S2 += sums[k][0];
+    const double scale = -1.0 / (0.69314718055994530942 * S2);
+    for (int64_t z = tid; z < dim; z += blockDim.x) {
+        double gx = 0.0, gy = 0.0;
+        for (int k = 0; k < GPC; ++k) {
+            const float2 v = s.gsmall[(size_t)k * dim + z];
+            gx += v.x;
+            gy += v.y;
+        }
+        if (s.grad) s.grad[z] = make_float2((float)(gx * scale), (float)(gy * scale));
+    }
+    if (tid == 0) m2_out[s.out_idx] = -log2(S2 / (double)dim);
+    __syncthreads();
+}
+
+template <int M>
+__device__ __forceinline__ bool large_task(const BatchedParams& B, const BatchState& s, int64_t local, float2* smem) {
+    const G3State S{s.psi, s.N, s.scratch, s.R, s.A, s.U, s.n_batches, s.p1, s.p2, s.p3,
+                    s.ctr, s.ctr + 64, s.ctr + 128};
+    const int64_t per_stage = (int64_t)s.p1 + s.p2 + s.p3;
+    const int64_t st = local / per_stage;
+    int r = (int)(local % per_stage);
+    int kind;
+    int64_t g;
+    if (r < s.p1) { kind = 1; g = st; }
+    else if (r < s.p1 + s.p2) { kind = 2; g = st - 1; r -= s.p1; }
+    else { kind = 3; g = st - 2; r -= s.p1 + s.p2; }
+    if (g < 0 || g >= s.n_batches) return true;
+    if (kind == 1) return g3_pass1<M>(S, B.ctl, g, r, smem);
+    if (kind == 2) {
+        double acc = 0.0, acc1 = 0.0;
+        return g3_pass2<M>(S, B.ctl, g, r, smem, acc, acc1, s.s2);
+    }
+    // pass 3 writes the shared partials: the previous large state must have released them
+    const unsigned* prev = s.prev_fin;
+    return g3_pass3<M>(S, B.ctl, g, r, smem, B.gpart + (size_t)blockIdx.x * B.dimmax, prev, prev ? s.prev_nfin : 0u);
+}
+
+__device__ __forceinline__ bool finalize_task(const BatchedParams& B, const BatchState& s, int f, double* m2_out,
+                                              int idx) {
+    // all pass-3 tasks of this state are done: every slot's counter reached its final value
+    for (int k = 0; k < s.R; ++k) {
+        const int64_t nb = (s.n_batches > k) ? (s.n_batches - k + s.R - 1) / s.R : 0;
+        if (!cta_wait_geq(s.ctr + 128 + k, (unsigned)(nb * s.p3) + B.ctl.wait_bias, B.ctl.status, B.ctl.spin_limit))
+            return false;
+    }
+    const int64_t dim = int64_t(1) << s.N;
+    const int64_t chunk = (dim + s.n_fin - 1) / s.n_fin;
+    const int64_t z0 = (int64_t)f * chunk, z1 = (z0 + chunk < dim) ? z0 + chunk : dim;
+    const double S2 = *reinterpret_cast<volatile double*>(s.s2);
+    const double scale = -1.0 / (0.69314718055994530942 * S2);
+    for (int64_t z = z0 + threadIdx.x; z < z1; z += blockDim.x) {
+        double gx = 0.0, gy = 0.0;
+        for (int k = 0; k < B.nparts; ++k) {
+            float2* p = B.gpart + (size_t)k * B.dimmax + z;
+            const float2 v = __ldcg(p);
+            gx += v.x;
+            gy += v.y;
+            __stcg(p, make_float2(0.f, 0.f));
+        }
+        if (s.grad) s.grad[z] = make_float2((float)(gx * scale), (float)(gy * scale));
+    }
+    if (threadIdx.x == 0 && f == 0) m2_out[s.out_idx] = -log2(S2 / (double)dim);
+    __syncthreads();
+    if (threadIdx.x == 0) { __threadfence(); red_release_add(s.fin, 1u); }
+    return true;
+}
+
+__global__ void __launch_bounds__(256, 2) batched_kernel(BatchedParams B) {
+    extern __shared__ float2 smem[];
+    __shared__ long long s_ticket;
+    const uint32_t tid = threadIdx.x;
+    for (;;) {
+        if (tid == 0) s_ticket = (long long)atomicAdd(B.ticket, 1ull);
+        __syncthreads();
+        const int64_t tau = s_ticket;
+        __syncthreads();
+        if (tau >= B.total) break;
+        int idx = 0;
+        while (idx + 1 < B.n_states && B.states[idx + 1].task_begin <= tau) ++idx;
+        const BatchState& s = B.states[idx];
+        const int64_t local = tau - s.task_begin;
+        bool ok = true;
+        if (s.kind == 0) {
+            switch (s.N) {
+                case 10: small_item<9>(s, smem, B.m2_out, idx); break;
+                case 11: small_item<10>(s, smem, B.m2_out, idx); break;
+                case 12: small_item<11>(s, smem, B.m2_out, idx); break;
+                case 13: small_item<12>(s, smem, B.m2_out, idx); break;
+                case 14: small_item<13>(s, smem, B.m2_out, idx); break;
+                default: break;
+            }
+        } else if (local < s.n_stage_tasks) {
+            switch (s.N) {
+                case 15: ok = large_task<4>(B, s, local, smem); break;
+                case 16: ok = large_task<5>(B, s, local, smem); break;
+                case 17: ok = large_task<6>(B, s, local, smem); break;
+                case 18: ok = large_task<7>(B, s, local, smem); break;
+                default: break;
+            }
+        } else {
+            ok = finalize_task(B, s, (int)(local - s.n_stage_tasks), B.m2_out, idx);
+        }
+        if (!ok) break;
+    }
+}
+
+size_t batched_smem_bytes() { return (size_t)tile_slots(13) * sizeof(float2); }
+
+cudaError_t batched_max_grid(int sm_count, int* grid) {
+    cudaError_t e = cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)batched_smem_bytes());
+    if (e != cudaSuccess) return e;
+    int occ = 0;
+    if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, batched_kernel, 256, batched_smem_bytes())) != cudaSuccess)
+        return e;
+    *grid = (occ < 1 ? 1 : occ) * sm_count;
+    return cudaSuccess;
+}
+
+cudaError_t launch_batched(const BatchedParams& B, int grid, cudaStream_t st) {
+    batched_kernel<<<grid, 256, batched_smem_bytes(), st>>>(B);
+    return cudaGetLastError();
+}
+
+}  // namespace hm

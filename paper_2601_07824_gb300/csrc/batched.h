@@ -1,0 +1,49 @@
+// batched.h -- launch interface of the batched persistent adjoint kernel (internal).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "grad_phases.cuh"
+
+namespace hm {
+
+struct BatchState {
+    const float2* psi;
+    float2* grad;              // dM_2/dpsi* out (complex64) or null
+    int N;
+    int kind;                  // 0: small (one CTA item), 1: large (three passes + finalize)
+    int out_idx;               // position of this state in the caller's arrays
+    int64_t task_begin;        // first ticket of this state's segment
+    // small states
+    float2* gsmall;            // GPC x 2^N partials, zeroed before launch
+    // large states
+    float2* scratch;           // R x A x 2^(N-1)
+    int R, A, U;
+    int64_t n_batches;
+    int p1, p2, p3;
+    int64_t n_stage_tasks;     // (n_batches + 2) * (p1 + p2 + p3)
+    int n_fin;                 // finalize tasks
+    unsigned* ctr;             // [64 done1][64 done2][64 done3], zeroed before launch
+    unsigned* fin;             // finalize tasks done (zeroed)
+    const unsigned* prev_fin;  // previous large state's fin counter, or null
+    unsigned prev_nfin;
+    double* s2;                // [S_2, S_1] accumulated with atomics (zeroed)
+};
+
+struct BatchedParams {
+    const BatchState* states;
+    int n_states;
+    int64_t total;             // total tickets
+    unsigned long long* ticket;
+    float2* gpart;             // per-CTA partial gradients [nparts][dimmax], zero on entry and exit
+    int64_t dimmax;
+    int nparts;                // = grid
+    double* m2_out;            // [n_states] (device)
+    G3Ctl ctl;
+};
+
+size_t batched_smem_bytes();
+cudaError_t batched_max_grid(int sm_count, int* grid);
+cudaError_t launch_batched(const BatchedParams& B, int grid, cudaStream_t st);
+
+}  // namespace hm

@@ -1,0 +1,212 @@
+// batched_api.cu -- hadamag_sre_batched: host planning, autotuning and launch of batched.cu.
+//
+// The autotuner picks, per set of state sizes (and gradient on/off), the number of X-strings
+// A that a pass-1 task of a large state covers (the x-batch: 8, 4 or 2), by timing one full
+// launch per candidate on the first uncaptured call and caching the fastest.  The pass-1 width
+// (10 bits) and the small/large split (N <= 14 one CTA per state) are fixed by the kernels.
+#include <algorithm>
+#include <cstring>
+#include <map>
+#include <string>
+#include <vector>
+
+#include "batched.h"
+#include "ctx.h"
+
+using namespace hm;
+
+namespace {
+
+struct Plan {
+    std::vector<BatchState> st;
+    int64_t total = 0;
+    size_t scratch_bytes = 0, gsmall_bytes = 0;
+    int n_large = 0;
+    int64_t dimmax = 1;
+};
+
+// Builds the state table (offsets into the context buffers are filled in later).
+Plan make_plan(int count, const void* const* psi, const int* N, void* const* grad, int A_large) {
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
+        const bool lx = N[x] >= 15, ly = N[y] >= 15;
+        if (lx != ly) return !lx;  // small states first (one long item each), then large
+        return N[x] > N[y];        // largest first
+    });
+    Plan p;
+    for (int i : order) {
+        BatchState s{};
+        s.psi = reinterpret_cast<const float2*>(psi[i]);
+        s.grad = grad ? reinterpret_cast<float2*>(grad[i]) : nullptr;
+        s.N = N[i];
+        s.task_begin = p.total;
+        s.out_idx = i;
+        const int64_t dim = int64_t(1) << s.N;
+        if (s.N <= 14) {
+            s.kind = 0;
+            p.gsmall_bytes += (size_t)(256 / (1 << (s.N - 6))) * dim * sizeof(float2);
+            p.total += 1;
+        } else {
+            s.kind = 1;
+            const int M = s.N - 11;
+            s.R = 3;
+            s.A = A_large;
+            s.U = 8 / s.A;
+            s.n_batches = dim / s.A;
+            s.p1 = (1 << M) / (s.U * 2);
+            s.p2 = s.A * (1024 >> (13 - M));
+            s.p3 = s.A * ((1 << M) / 16);
+            s.n_stage_tasks = (s.n_batches + 2) * ((int64_t)s.p1 + s.p2 + s.p3);
+            s.n_fin = (int)std::max<int64_t>(1, dim / 2048);
+            p.scratch_bytes += (size_t)s.R * s.A * (size_t)(dim / 2) * sizeof(float2);
+            p.total += s.n_stage_tasks + s.n_fin;
+            p.n_large++;
+            p.dimmax = std::max(p.dimmax, dim);
+        }
+        p.st.push_back(s);
+    }
+    return p;
+}
+
+struct TuneKey {
+    std::string key;
+};
+
+std::string tune_key(int count, const int* N, int want_grad) {
+    std::vector<int> v(N, N + count);
+    std::sort(v.begin(), v.end());
+    std::string k = want_grad ? "g" : "f";
+    for (int n : v) k += "," + std::to_string(n);
+    return k;
+}
+
+std::map<std::string, int>& tune_cache() {
+    static std::map<std::string, int> m;
+    return m;
+}
+
+hadamag_status run(hadamag_ctx_t c, int count, const void* const* psi, const int* N, int want_grad,
+                   void* const* grad, double* m2, cudaStream_t st, int A_large) {
+    hadamag_status s;
+    cudaError_t e;
+    Plan p = make_plan(count, psi, N, want_grad ? grad : nullptr, A_large);
+    const int ns = (int)p.st.size();
+    int grid = 0;
+    if ((e = batched_max_grid(c->sm_count, &grid)) != cudaSuccess) return cuda_fail(c, e, "occupancy");
+    // one device allocation carved into: table | counters | s2 | ticket (buffers below separately)
+    const size_t table_bytes = (size_t)ns * sizeof(BatchState);
+    const size_t ctr_bytes = (size_t)ns * 256 * sizeof(unsigned);
+    const size_t s2_bytes = (size_t)ns * 2 * sizeof(double);
+    const size_t meta_bytes = table_bytes + ctr_bytes + s2_bytes + 256;
+    if ((s = ensure_buf(c, c->batch_meta, meta_bytes))) return s;
+    if ((s = ensure_buf(c, c->scratch, std::max<size_t>(p.scratch_bytes, 256)))) return s;
+    if ((s = ensure_buf(c, c->batch_sums, std::max<size_t>(p.gsmall_bytes, 256)))) return s;
+    const size_t gpart_bytes = p.n_large ? (size_t)grid * p.dimmax * sizeof(float2) : 256;
+    if ((s = ensure_buf(c, c->grad_acc, gpart_bytes))) return s;
+    if (c->host_table_bytes < table_bytes) {
+        if (c->host_table) cudaFreeHost(c->host_table);
+        c->host_table = nullptr;
+        c->host_table_bytes = 0;
+        if (cudaMallocHost(&c->host_table, table_bytes) != cudaSuccess) return fail(c, HADAMAG_ERR_OOM, "pinned table");
+        c->host_table_bytes = table_bytes;
+    }
+    char* meta = (char*)c->batch_meta.ptr;
+    unsigned* ctr = (unsigned*)(meta + table_bytes);
+    double* s2 = (double*)(meta + table_bytes + ctr_bytes);
+    unsigned long long* ticket = (unsigned long long*)(meta + table_bytes + ctr_bytes + s2_bytes);
+    size_t soff = 0, goff = 0;
+    const unsigned* prev_fin = nullptr;
+    unsigned prev_nfin = 0;
+    for (int k = 0; k < ns; ++k) {
+        BatchState& b = p.st[k];
+        b.ctr = ctr + (size_t)k * 256;
+        b.fin = b.ctr + 192;
+        b.s2 = s2 + 2 * k;
+        if (b.kind == 0) {
+            b.gsmall = (float2*)((char*)c->batch_sums.ptr + goff);
+            goff += (size_t)(256 / (1 << (b.N - 6))) * ((size_t)1 << b.N) * sizeof(float2);
+        } else {
+            b.scratch = (float2*)((char*)c->scratch.ptr + soff);
+            soff += (size_t)b.R * b.A * ((size_t)1 << (b.N - 1)) * sizeof(float2);
+            b.prev_fin = prev_fin;
+            b.prev_nfin = prev_nfin;
+            prev_fin = b.fin;
+            prev_nfin = (unsigned)b.n_fin;
+        }
+    }
+    std::memcpy(c->host_table, p.st.data(), table_bytes);
+    if ((e = cudaMemcpyAsync(meta, c->host_table, table_bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+        return cuda_fail(c, e, "copy table");
+    if ((e = cudaMemsetAsync(ctr, 0, ctr_bytes + s2_bytes + 256, st)) != cudaSuccess) return cuda_fail(c, e, "memset");
+    if (p.gsmall_bytes && (e = cudaMemsetAsync(c->batch_sums.ptr, 0, p.gsmall_bytes, st)) != cudaSuccess)
+        return cuda_fail(c, e, "memset");
+    if (p.n_large && (e = cudaMemsetAsync(c->grad_acc.ptr, 0, gpart_bytes, st)) != cudaSuccess)
+        return cuda_fail(c, e, "memset");
+    BatchedParams B{};
+    B.states = (const BatchState*)meta;
+    B.n_states = ns;
+    B.total = p.total;
+    B.ticket = ticket;
+    B.gpart = (float2*)c->grad_acc.ptr;
+    B.dimmax = p.dimmax;
+    B.nparts = grid;
+    B.m2_out = m2;
+    B.ctl = G3Ctl{(int*)c->status.ptr, c->spin_limit, c->wait_bias};
+    e = launch_batched(B, grid, st);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(c, e, "batched_kernel");
+    return HADAMAG_OK;
+}
+
+}  // namespace
+
+extern "C" hadamag_status hadamag_sre_batched(hadamag_ctx_t c, int count, const void* const* psi, const int* N,
+                                              int want_grad, void* const* grad, double* m2, hadamag_stream_t stream) {
+    if (!c) return HADAMAG_ERR_INVALID_ARG;
+    if (count < 1 || !psi || !N || !m2 || (want_grad && !grad))
+        return fail(c, HADAMAG_ERR_INVALID_ARG, "bad batch arguments");
+    for (int i = 0; i < count; ++i) {
+        if (N[i] < 10 || N[i] > 18) return fail(c, HADAMAG_ERR_INVALID_ARG, "batched states need 10 <= N <= 18");
+        if (!aligned16(psi[i]) || (want_grad && !aligned16(grad[i])))
+            return fail(c, HADAMAG_ERR_INVALID_ARG, "null or misaligned pointer in batch");
+    }
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    c->last_error[0] = 0;
+    cudaError_t e = cudaSetDevice(c->device);
+    if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
+    if ((e = cudaMemsetAsync(c->status.ptr, 0, sizeof(int), st)) != cudaSuccess) return cuda_fail(c, e, "memset");
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if ((e = cudaStreamIsCapturing(st, &cap)) != cudaSuccess) return cuda_fail(c, e, "capture query");
+    const std::string key = tune_key(count, N, want_grad);
+    auto it = tune_cache().find(key);
+    int A = 8;
+    if (it != tune_cache().end()) {
+        A = it->second;
+    } else if (cap == cudaStreamCaptureStatusNone && c->autotune) {
+        // time one launch per candidate x-batch, keep the fastest
+        float best = 1e30f;
+        cudaEvent_t e0, e1;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return fail(c, HADAMAG_ERR_CUDA, "events");
+        for (int cand : {8, 4, 2}) {
+            cudaEventRecord(e0, st);
+            hadamag_status s = run(c, count, psi, N, want_grad, grad, m2, st, cand);
+            if (s) { cudaEventDestroy(e0); cudaEventDestroy(e1); return s; }
+            cudaEventRecord(e1, st);
+            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return cuda_fail(c, e, "tune sync");
+            float ms = 0.f;
+            cudaEventElapsedTime(&ms, e0, e1);
+            if (ms < best) { best = ms; A = cand; }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+        tune_cache()[key] = A;
+    }
+    return run(c, count, psi, N, want_grad, grad, m2, st, A);
+}
+
+extern "C" hadamag_status hadamag_batched_status(hadamag_ctx_t c, hadamag_stream_t stream) {
+    if (!c) return HADAMAG_ERR_INVALID_ARG;
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    return finish(c, nullptr, 0, st);
+}

@@ -89,9 +89,17 @@ struct TileSched {
     static constexpr int last_shift() { return shift(NR - 1); }
 };
 
+struct PadAddr {  // padded placement (conflict-free for every register window)
+    __device__ __forceinline__ uint32_t operator()(uint32_t j) const { return swz(j); }
+};
+struct DenseAddr {  // dense placement (conflict-free when lanes run over the low tile bits)
+    __device__ __forceinline__ uint32_t operator()(uint32_t j) const { return j; }
+};
+
 // Rounds 1..NR-1: exchange through shared memory, then butterflies on the new bits.
-template <int B, int LO, int E, int R, class Sync>
-__device__ __forceinline__ void tile_rounds(float2 (&x)[1 << E], float2* sm, uint32_t t, Sync sync) {
+template <int B, int LO, int E, int R, class Sync, class Addr = PadAddr>
+__device__ __forceinline__ void tile_rounds(float2 (&x)[1 << E], float2* sm, uint32_t t, Sync sync,
+                                            Addr addr = Addr()) {
     using S = TileSched<B, LO, E>;
     if constexpr (R < S::NR) {
         constexpr int sp = S::shift(R - 1);
@@ -99,14 +107,29 @@ __device__ __forceinline__ void tile_rounds(float2 (&x)[1 << E], float2* sm, uin
         constexpr int hi = (s + E < S::S0) ? (s + E) : S::S0;
         sync();
 #pragma unroll
-        for (int i = 0; i < (1 << E); ++i) sm[swz(deposit<E>(t, i, sp))] = x[i];
+        for (int i = 0; i < (1 << E); ++i) sm[addr(deposit<E>(t, i, sp))] = x[i];
         sync();
 #pragma unroll
-        for (int i = 0; i < (1 << E); ++i) x[i] = sm[swz(deposit<E>(t, i, s))];
+        for (int i = 0; i < (1 << E); ++i) x[i] = sm[addr(deposit<E>(t, i, s))];
         reg_fwht<E, 0, hi - s>(x);
-        tile_rounds<B, LO, E, R + 1>(x, sm, t, sync);
+        tile_rounds<B, LO, E, R + 1>(x, sm, t, sync, addr);
     }
 }
+
+// Named barrier over `N` threads (id > 0; id 0 is __syncthreads).
+template <int ID, int NTHR>
+struct SyncNamed {
+    __device__ __forceinline__ void operator()() const { asm volatile("bar.sync %0, %1;" ::"n"(ID), "n"(NTHR) : "memory"); }
+};
+
+// cp.async (LDGSTS) 16-byte global -> shared copies, L2 only.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+    const uint32_t d = (uint32_t)__cvta_generic_to_shared(smem_dst);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int NPEND>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(NPEND) : "memory"); }
 
 // ---- reductions -----------------------------------------------------------------------
 // Per-element terms of sum_b |c|^{2n}: the kernels accumulate, per complex W value,
@@ -210,6 +233,45 @@ __device__ __forceinline__ bool cta_wait_geq(const unsigned* ctr, unsigned targe
     int r = ok;
     __syncthreads();
     return r != 0;
+}
+
+// Like cta_wait_geq for a group of threads that synchronise with barrier `Sync`; `leader`
+// is the thread that polls.
+template <class Sync>
+__device__ __forceinline__ bool group_wait_geq(const unsigned* ctr, unsigned target, int* status, long long limit,
+                                               unsigned seen, bool leader, int* flag, Sync sync) {
+    if (leader) {
+        long long it = 0;
+        int good = 1;
+        if (seen >= target) fence_acquire();
+        else while (ld_acquire(ctr) < target) {
+            if (ld_status(status) != 0) { good = 0; break; }
+            if (++it > limit) { atomicOr(status, ST_TIMEOUT); good = 0; break; }
+            __nanosleep(100);
+        }
+        if (good && ld_status(status) != 0) good = 0;
+        *flag = good;
+    }
+    sync();
+    const int r = *flag;
+    sync();
+    return r != 0;
+}
+
+// Warp version: lane 0 polls, the warp converges with __syncwarp.
+__device__ __forceinline__ bool warp_wait_geq(const unsigned* ctr, unsigned target, int* status, long long limit) {
+    int good = 1;
+    if ((threadIdx.x & 31) == 0) {
+        long long it = 0;
+        while (ld_acquire(ctr) < target) {
+            if (ld_status(status) != 0) { good = 0; break; }
+            if (++it > limit) { atomicOr(status, ST_TIMEOUT); good = 0; break; }
+            __nanosleep(100);
+        }
+        if (good && ld_status(status) != 0) good = 0;
+    }
+    good = __shfl_sync(0xffffffffu, good, 0);
+    return good != 0;
 }
 
 }  // namespace hm

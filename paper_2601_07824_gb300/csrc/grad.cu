@@ -18,118 +18,24 @@
 // update their own partial without atomics.  Partials are summed in a fixed order in FP64.
 #include "common.cuh"
 #include "grad.h"
-#include "pairs.cuh"
+#include "grad_phases.cuh"
 
 namespace hm {
-
-__device__ __forceinline__ float2 cube_parts(float2 w) {
-    return make_float2(w.x * w.x * w.x, w.y * w.y * w.y);
-}
-
-// Adds the pair contributions of Q(j) for tile index z' = j to the partial gradient gp.
-__device__ __forceinline__ void scatter_pair(float2* __restrict__ gp, const float2* __restrict__ psi, int64_t z,
-                                             int64_t zb, float2 q) {
-    // gp[z] += 32 psi[zb] Q,  gp[zb] += 32 psi[z] conj(Q)
-    const float2 pz = ld_amp(psi, z), pb = ld_amp(psi, zb);
-    float2 g0 = gp[z], g1 = gp[zb];
-    g0.x += 32.f * (pb.x * q.x - pb.y * q.y);
-    g0.y += 32.f * (pb.x * q.y + pb.y * q.x);
-    g1.x += 32.f * (pz.x * q.x + pz.y * q.y);
-    g1.y += 32.f * (pz.y * q.x - pz.x * q.y);
-    gp[z] = g0;
-    gp[zb] = g1;
-}
-__device__ __forceinline__ void scatter_zero(float2* __restrict__ gp, const float2* __restrict__ psi, int64_t z,
-                                             float2 q) {
-    const float2 p0 = ld_amp(psi, z), p1 = ld_amp(psi, z + 1);
-    const float e = 32.f * (q.x + q.y), o = 32.f * (q.x - q.y);
-    float2 g0 = gp[z], g1 = gp[z + 1];
-    g0.x += e * p0.x; g0.y += e * p0.y;
-    g1.x += o * p1.x; g1.y += o * p1.y;
-    gp[z] = g0;
-    gp[z + 1] = g1;
-}
 
 // ------------------------------------------------------------------------------------------
 template <int L>
 __global__ void __launch_bounds__(OnepassShape<L>::NT)
 grad_onepass(const float2* __restrict__ psi, int N, double* __restrict__ sums, float2* __restrict__ gpart) {
     using Sh = OnepassShape<L>;
-    constexpr int E = Sh::E, G = Sh::G, GPC = Sh::GPC;
-    using S = TileSched<L, 0, E>;
-    constexpr int SL = S::last_shift();
+    constexpr int G = Sh::G, GPC = Sh::GPC;
     extern __shared__ float2 smem[];
-    __shared__ float red[16][2];
     const uint32_t tid = threadIdx.x, gi = tid / G, t = tid % G;
     float2* sm = smem + (size_t)gi * (L >= 5 ? tile_slots(L) : (1u << L));
     const int64_t ngroups = (int64_t)gridDim.x * GPC;
     const int64_t gg = (int64_t)blockIdx.x * GPC + gi;
     const int64_t dim = int64_t(1) << N;
-    const int64_t iters = (dim + ngroups - 1) / ngroups;
-    float2* gp = gpart + (size_t)gg * dim;
     double acc = 0.0, acc1 = 0.0;
-    for (int64_t it = 0; it < iters; ++it) {
-        const int64_t a = gg + it * ngroups;
-        const bool valid = a < dim;
-        const int64_t av = valid ? a : 0;
-        const int p = av ? msb64(av) : 0;
-        float2 x[1 << E];
-#pragma unroll
-        for (int i = 0; i < (1 << E); ++i) x[i] = pair_product(psi, deposit<E>(t, i, S::S0), av, p);
-        reg_fwht<E, 0, E>(x);
-        if constexpr (G <= 32) tile_rounds<L, 0, E, 1>(x, sm, t, SyncWarp());
-        else tile_rounds<L, 0, E, 1>(x, sm, t, SyncCta());
-        // S_2 and S_1 terms, then Y = R^3 + i I^3 back to the round-0 layout
-        float q = 0.f, s1 = 0.f;
-#pragma unroll
-        for (int i = 0; i < (1 << E); ++i) {
-            const float2 sq = mul2(x[i], x[i]);
-            s1 += sq.x + sq.y;
-            q = fmaf(sq.x, sq.x, fmaf(sq.y, sq.y, q));
-            x[i] = cube_parts(x[i]);
-        }
-        if constexpr (L >= 5) {
-            if constexpr (G <= 32) __syncwarp(); else __syncthreads();
-#pragma unroll
-            for (int i = 0; i < (1 << E); ++i) sm[swz(deposit<E>(t, i, SL))] = x[i];
-            if constexpr (G <= 32) __syncwarp(); else __syncthreads();
-#pragma unroll
-            for (int i = 0; i < (1 << E); ++i) x[i] = sm[swz(deposit<E>(t, i, S::S0))];
-        }
-        reg_fwht<E, 0, E>(x);
-        if constexpr (G <= 32) tile_rounds<L, 0, E, 1>(x, sm, t, SyncWarp());
-        else tile_rounds<L, 0, E, 1>(x, sm, t, SyncCta());
-        if (valid) {
-#pragma unroll
-            for (int i = 0; i < (1 << E); ++i) {
-                const int64_t zp = deposit<E>(t, i, SL);
-                if (av != 0) {
-                    const int64_t z = insert0(zp, p);
-                    scatter_pair(gp, psi, z, z ^ av, x[i]);
-                } else {
-                    scatter_zero(gp, psi, zp << 1, x[i]);
-                }
-            }
-        }
-        // group sums of |c|^4 = 16 (R^4 + I^4) and |c|^2 = 4 (R^2 + I^2)
-        if constexpr (G <= 32) {
-#pragma unroll
-            for (int o = 16; o >= 1; o >>= 1)
-                if (o < G) { q += __shfl_xor_sync(0xffffffffu, q, o); s1 += __shfl_xor_sync(0xffffffffu, s1, o); }
-        } else {
-#pragma unroll
-            for (int o = 16; o >= 1; o >>= 1) { q += __shfl_xor_sync(0xffffffffu, q, o); s1 += __shfl_xor_sync(0xffffffffu, s1, o); }
-            if ((tid & 31) == 0) { red[tid >> 5][0] = q; red[tid >> 5][1] = s1; }
-            __syncthreads();
-            if (tid == 0) {
-                float a0 = 0.f, a1 = 0.f;
-                for (int w = 0; w < (G >> 5); ++w) { a0 += red[w][0]; a1 += red[w][1]; }
-                q = a0; s1 = a1;
-            }
-            __syncthreads();
-        }
-        if (t == 0 && valid) { acc += 16.0 * (double)q; acc1 += 4.0 * (double)s1; }
-    }
+    grad_onepass_group<L>(psi, N, gpart + (size_t)gg * dim, gg, ngroups, sm, acc, acc1);
     if (t == 0) {
         sums[gg * 3 + 0] = acc;
         sums[gg * 3 + 1] = acc1;
@@ -141,20 +47,15 @@ grad_onepass(const float2* __restrict__ psi, int N, double* __restrict__ sums, f
 // Three-pass persistent kernel (K1 = 10, M = N - 11), 256 threads, two CTAs per SM.
 template <int M>
 __global__ void __launch_bounds__(256, 2) grad_threepass(GradParams P) {
-    using Sh = TwoPassShape<10, M>;
-    constexpr int K1 = 10, L = Sh::L, LOGT = Sh::LOGT, T = Sh::T, TILES = Sh::TILES;
-    using S2 = TileSched<13, LOGT, 5>;
-    constexpr int SL2 = S2::last_shift();
     extern __shared__ float2 smem[];
-    __shared__ float red[8][2];
-    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const float2* __restrict__ psi = P.psi;
+    const uint32_t tid = threadIdx.x;
+    const G3State S{P.psi, P.N, P.scratch, P.R, P.A, P.U, P.n_batches, P.p1, P.p2, P.p3, P.done1, P.done2, P.done3};
+    const G3Ctl C{P.status, P.spin_limit, P.wait_bias};
     const int64_t dim = int64_t(1) << P.N;
     const int64_t per_stage = (int64_t)P.p1 + P.p2 + P.p3;
     const int64_t total = (P.n_batches + 2) * per_stage;
     float2* gp = P.gpart + (size_t)blockIdx.x * dim;
     double acc = 0.0, acc1 = 0.0;
-
     for (int64_t task = blockIdx.x; task < total; task += gridDim.x) {
         // stage s: pass 1 of batch s, pass 2 of batch s-1, pass 3 of batch s-2
         const int64_t s = task / per_stage;
@@ -165,120 +66,11 @@ __global__ void __launch_bounds__(256, 2) grad_threepass(GradParams P) {
         else if (r < P.p1 + P.p2) { kind = 2; g = s - 1; r -= P.p1; }
         else { kind = 3; g = s - 2; r -= P.p1 + P.p2; }
         if (g < 0 || g >= P.n_batches) continue;  // CTA-uniform
-        const int slot = (int)(g % P.R);
-        float2* sbase = P.scratch + (size_t)slot * P.A * ((size_t)1 << L);
-
-        if (kind == 1) {
-            if (g >= P.R && !cta_wait_geq(P.done3 + slot, (unsigned)((g / P.R) * P.p3) + P.wait_bias, P.status, P.spin_limit))
-                return;
-            const int a_idx = warp % P.A;
-            const int64_t unit = ((int64_t)r * P.U + warp / P.A) * 2;
-            const int64_t a = g * P.A + a_idx;
-            if (a < dim) {
-                float2* sm = smem + warp * tile_slots(10);
-                float2 x[32];
-                for (int uu = 0; uu < 2; ++uu) {
-                    const PairRows<K1, M> pr(a, unit + uu);
-                    float2* dst = sbase + (size_t)a_idx * ((size_t)1 << L) + ((size_t)(unit + uu) << K1);
-#pragma unroll
-                    for (int k = 0; k < 32; ++k) x[k] = pr.value(psi, a, lane | (k << 5));
-                    reg_fwht<5, 0, 5>(x);
-                    tile_rounds<10, 0, 5, 1>(x, sm, lane, SyncWarp());
-#pragma unroll
-                    for (int k = 0; k < 32; ++k) __stcg(dst + lane + (k << 5), x[k]);
-                }
-            }
-            __syncthreads();
-            if (tid == 0) { __threadfence(); red_release_add(P.done1 + slot, 1u); }
-        } else if (kind == 2) {
-            if (!cta_wait_geq(P.done1 + slot, (unsigned)((g / P.R + 1) * P.p1) + P.wait_bias, P.status, P.spin_limit))
-                return;
-            const int a_idx = r / TILES, tile = r % TILES;
-            const int64_t a = g * P.A + a_idx;
-            if (a < dim) {
-                float2* src = sbase + (size_t)a_idx * ((size_t)1 << L) + (size_t)tile * T;
-                float2 x[32];
-#pragma unroll
-                for (int k = 0; k < 32; ++k) {
-                    const uint32_t j = deposit<5>(tid, k, 8);
-                    x[k] = __ldcg(src + ((size_t)(j >> LOGT) << K1) + (j & (T - 1)));
-                }
-                reg_fwht<5, 0, 5>(x);
-                tile_rounds<13, LOGT, 5, 1>(x, smem, tid, SyncCta());
-                float q = 0.f, s1 = 0.f;
-#pragma unroll
-                for (int k = 0; k < 32; ++k) {
-                    const float2 sq = mul2(x[k], x[k]);
-                    s1 += sq.x + sq.y;
-                    q = fmaf(sq.x, sq.x, fmaf(sq.y, sq.y, q));
-                    x[k] = cube_parts(x[k]);
-                }
-                // back to the round-0 layout, transform the high bits again, store in place
-                __syncthreads();
-#pragma unroll
-                for (int k = 0; k < 32; ++k) smem[swz(deposit<5>(tid, k, SL2))] = x[k];
-                __syncthreads();
-#pragma unroll
-                for (int k = 0; k < 32; ++k) x[k] = smem[swz(deposit<5>(tid, k, 8))];
-                reg_fwht<5, 0, 5>(x);
-                tile_rounds<13, LOGT, 5, 1>(x, smem, tid, SyncCta());
-#pragma unroll
-                for (int k = 0; k < 32; ++k) {
-                    const uint32_t j = deposit<5>(tid, k, SL2);
-                    __stcg(src + ((size_t)(j >> LOGT) << K1) + (j & (T - 1)), x[k]);
-                }
-#pragma unroll
-                for (int o = 16; o >= 1; o >>= 1) { q += __shfl_xor_sync(0xffffffffu, q, o); s1 += __shfl_xor_sync(0xffffffffu, s1, o); }
-                if (lane == 0) { red[warp][0] = q; red[warp][1] = s1; }
-                __syncthreads();
-                if (tid == 0)
-                    for (int w = 0; w < 8; ++w) { acc += 16.0 * (double)red[w][0]; acc1 += 4.0 * (double)red[w][1]; }
-            }
-            __syncthreads();
-            if (tid == 0) { __threadfence(); red_release_add(P.done2 + slot, 1u); }
-        } else {
-            if (!cta_wait_geq(P.done2 + slot, (unsigned)((g / P.R + 1) * P.p2) + P.wait_bias, P.status, P.spin_limit))
-                return;
-            // one X-string, 16 units (two per warp): its pairs touch every entry at most once
-            const int per_a = (1 << M) / 16;
-            const int a_idx = r / per_a;
-            const int64_t unit0 = (int64_t)(r % per_a) * 16 + warp * 2;
-            const int64_t a = g * P.A + a_idx;
-            if (a < dim) {
-                float2* sm = smem + warp * tile_slots(10);
-                float2 x[32];
-                for (int uu = 0; uu < 2; ++uu) {
-                    const int64_t unit = unit0 + uu;
-                    const float2* src = sbase + (size_t)a_idx * ((size_t)1 << L) + ((size_t)unit << K1);
-                    // column (k<<5)|lane holds tile index j = k | (lane<<5); with j' = swap of the
-                    // two 5-bit halves this is the round-0 layout of the 10-bit schedule
-#pragma unroll
-                    for (int k = 0; k < 32; ++k) x[k] = __ldcg(src + lane + (k << 5));
-                    reg_fwht<5, 0, 5>(x);
-                    tile_rounds<10, 0, 5, 1>(x, sm, lane, SyncWarp());
-                    // now register k holds Q at j = lane | (k << 5) (the pair-product layout)
-                    const PairRows<K1, M> pr(a, unit);
-#pragma unroll
-                    for (int k = 0; k < 32; ++k) {
-                        const uint32_t j = lane | (k << 5);
-                        if (a >> K1) {
-                            scatter_pair(gp, psi, pr.rowA + j, pr.rowB + (int64_t)(j ^ (uint32_t)pr.al), x[k]);
-                        } else {
-                            const int64_t row = (j >> (K1 - 1)) ? pr.rowB : pr.rowA;
-                            const int64_t lp = j & ((1u << (K1 - 1)) - 1u);
-                            if (a != 0) {
-                                const int64_t z = row + insert0(lp, pr.p);
-                                scatter_pair(gp, psi, z, z ^ a, x[k]);
-                            } else {
-                                scatter_zero(gp, psi, row + (lp << 1), x[k]);
-                            }
-                        }
-                    }
-                }
-            }
-            __syncthreads();
-            if (tid == 0) red_release_add(P.done3 + slot, 1u);
-        }
+        bool ok;
+        if (kind == 1) ok = g3_pass1<M>(S, C, g, r, smem);
+        else if (kind == 2) ok = g3_pass2<M>(S, C, g, r, smem, acc, acc1);
+        else ok = g3_pass3<M>(S, C, g, r, smem, gp);
+        if (!ok) return;
     }
     if (tid == 0) {
         P.sums[blockIdx.x * 3 + 0] = acc;

@@ -45,6 +45,49 @@ struct TwoPassParams {
     int per_a;
 };
 
+// Warp-specialised persistent kernel (16 <= N <= 20): pass-1 warps and a pass-2 group per SM.
+struct WsParams {
+    const float2* psi;
+    int N;
+    double nq;
+    int64_t count;
+    const int64_t* a_list;
+    float2* scratch;         // R slots x A X-strings x 2^(N-1) values
+    int R, A;
+    int64_t n_batches;
+    int p1, p2;              // pass-1 warp tasks / pass-2 tiles per batch
+    unsigned* done1;
+    unsigned* done2;
+    int* status;
+    long long spin_limit;
+    unsigned wait_bias;
+    double* out;
+    int per_a;
+};
+int ws_tiles_per_a(int N);
+cudaError_t launch_ws(const WsParams& P, int mode, int grid, cudaStream_t st);
+
+// Three-pass per-X-string kernel for 25 <= N <= 28 (scratch in HBM), one X-string per batch.
+struct HbmParams {
+    const float2* psi;
+    int N;
+    int64_t count;
+    const int64_t* a_list;
+    float2* scratch;         // R slots x 2^(N-1) values
+    int R;
+    int64_t n_batches;
+    int p1, p2, p3;          // tasks per batch (2^(N-14) each)
+    unsigned* done1;
+    unsigned* done2;
+    unsigned* done3;
+    int* status;
+    long long spin_limit;
+    unsigned wait_bias;
+    double* out;             // [count][tiles][3]
+};
+int hbm_tiles_per_a(int N);
+cudaError_t launch_hbm(const HbmParams& P, int sm_count, int* grid, cudaStream_t st);
+
 // Two-pass geometry for N in [16, 24]: pass 1 transforms K1 = twopass_k1(N) bits (10 or 13),
 // pass 2 the other N-1-K1 bits, in tiles of 2^13 values; tiles per X-string:
 int twopass_tiles_per_a(int N);

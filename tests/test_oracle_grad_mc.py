@@ -77,10 +77,27 @@ def test_mc_identity_list_reduces_to_exact():
 
 def test_mc_estimate_within_band():
     N = 12
-    psi = I.brickwork_haar(N, 4, seed=7, dtype=np.complex128)
+    psi = I.gaussian_state(N, 7)
     exact = f(psi)
     M, se, S = oracle.sre_mc(psi, 512, seed=99)
     assert se > 0
     assert abs(M - exact) < 4 * se + 1e-12, (M, exact, se)
     a = oracle.mc_xstrings(99, 512, N)
     assert np.allclose(S, oracle.sre_terms_list(psi, a), rtol=1e-15)
+
+
+def test_mc_estimator_treats_identity_row_exactly():
+    # Sec. 4.2 footnote: the identity is handled exactly, not sampled.  With the X-string a = 0
+    # evaluated exactly, S_hat = [S(0) + (2^N - 1) mean_{a_i != 0} S(a_i)] / 2^N.
+    N = 6
+    psi = I.gaussian_state(N, 3)
+    M, se, S = oracle.sre_mc(psi, 300, seed=5)
+    a = oracle.mc_xstrings(5, 300, N)
+    Sq, _, _ = oracle.sre_terms(psi, 2.0)
+    nz = a != 0
+    Shat = Sq[0] / 2 ** N + (2 ** N - 1) / 2 ** N * S[nz].mean()
+    assert abs(M + np.log2(Shat)) < 1e-12
+    # every a != 0 drawn once each -> exact
+    exact = f(psi)
+    Shat_all = Sq[0] / 2 ** N + (2 ** N - 1) / 2 ** N * Sq[1:].mean()
+    assert abs(-np.log2(Shat_all) - exact) < 1e-12
