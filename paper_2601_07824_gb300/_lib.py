@@ -117,6 +117,7 @@ class Context:
 
     def set_path(self, path: int):
         self.check(self.lib.hadamag_set_path(self.h, int(path)), "hadamag_set_path")
+        self.path = int(path)
 
     def set_wait_limit(self, spins: int, bias: int = 0):
         self.check(self.lib.hadamag_set_wait_limit(self.h, int(spins), int(bias)), "hadamag_set_wait_limit")

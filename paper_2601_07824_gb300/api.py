@@ -5,6 +5,7 @@ enqueued on torch's current stream of the tensor's device.
 """
 from __future__ import annotations
 
+import contextlib
 import ctypes
 
 import numpy as np
@@ -46,15 +47,31 @@ def _ctx(t: torch.Tensor):
     return context(t.device.index if t.device.index is not None else torch.cuda.current_device())
 
 
+@contextlib.contextmanager
+def _path(c, path):
+    """Select the transform path of context `c` for one call (None: keep the context's)."""
+    if path is None:
+        yield
+        return
+    prev = getattr(c, "path", PATH_AUTO)
+    c.set_path(path)
+    try:
+        yield
+    finally:
+        c.set_path(prev)
+
+
 def sre(psi: torch.Tensor, n: float = 2.0, path: int | None = None):
-    """(M_n, lost_norm): exact SRE, Eq. (sre), by the per-X-string Walsh-Hadamard method."""
+    """(M_n, lost_norm): exact SRE, Eq. (sre), by the per-X-string Walsh-Hadamard method.
+
+    path: None (the context's setting), PATH_CUDACORE, or PATH_TENSOR (tcgen05 +-1 Hadamard
+    blocks on fp16 hi/lo operands, used for 21 <= N <= 24) -- for this call only."""
     N = _check_state(psi)
     c = _ctx(psi)
-    if path is not None:
-        c.set_path(path)
     M, ln = ctypes.c_double(), ctypes.c_double()
-    c.check(c.lib.hadamag_sre(c.h, ctypes.c_void_p(psi.data_ptr()), N, float(n), _dtype_code(psi),
-                              ctypes.byref(M), ctypes.byref(ln), _stream(psi)), "hadamag_sre")
+    with _path(c, path):
+        c.check(c.lib.hadamag_sre(c.h, ctypes.c_void_p(psi.data_ptr()), N, float(n), _dtype_code(psi),
+                                  ctypes.byref(M), ctypes.byref(ln), _stream(psi)), "hadamag_sre")
     return M.value, ln.value
 
 
@@ -77,16 +94,17 @@ def sre_host(psi: np.ndarray, n: float = 2.0, device: int = 0):
     return M.value, ln.value
 
 
-def sre_terms(psi: torch.Tensor, n: float, a_list: torch.Tensor) -> torch.Tensor:
+def sre_terms(psi: torch.Tensor, n: float, a_list: torch.Tensor, path: int | None = None) -> torch.Tensor:
     """Per-X-string sums [sum_b |chi|^{2n}, sum_b |chi|^2, sum_b |chi|^2 log2 |chi|^2] (count x 3)."""
     N = _check_state(psi)
     if a_list.dtype != torch.int64 or a_list.device != psi.device or not a_list.is_contiguous():
         raise ValueError("a_list must be a contiguous int64 tensor on the state's device")
     out = torch.empty((a_list.numel(), 3), dtype=torch.float64, device=psi.device)
     c = _ctx(psi)
-    c.check(c.lib.hadamag_sre_terms(c.h, ctypes.c_void_p(psi.data_ptr()), N, float(n), _dtype_code(psi),
-                                    ctypes.c_void_p(a_list.data_ptr()), a_list.numel(),
-                                    ctypes.c_void_p(out.data_ptr()), _stream(psi)), "hadamag_sre_terms")
+    with _path(c, path):
+        c.check(c.lib.hadamag_sre_terms(c.h, ctypes.c_void_p(psi.data_ptr()), N, float(n), _dtype_code(psi),
+                                        ctypes.c_void_p(a_list.data_ptr()), a_list.numel(),
+                                        ctypes.c_void_p(out.data_ptr()), _stream(psi)), "hadamag_sre_terms")
     return out
 
 
@@ -99,14 +117,15 @@ def mc_xstrings(seed: int, count: int, N: int, device: int = 0) -> torch.Tensor:
     return out
 
 
-def sre_mc(psi: torch.Tensor, samples: int, seed: int):
+def sre_mc(psi: torch.Tensor, samples: int, seed: int, path: int | None = None):
     """(M2_hat, stderr) of the uniform-X Monte-Carlo estimator."""
     N = _check_state(psi)
     c = _ctx(psi)
     M, se = ctypes.c_double(), ctypes.c_double()
-    c.check(c.lib.hadamag_sre_mc(c.h, ctypes.c_void_p(psi.data_ptr()), N, int(samples),
-                                 ctypes.c_uint64(seed & (2 ** 64 - 1)), _dtype_code(psi),
-                                 ctypes.byref(M), ctypes.byref(se), _stream(psi)), "hadamag_sre_mc")
+    with _path(c, path):
+        c.check(c.lib.hadamag_sre_mc(c.h, ctypes.c_void_p(psi.data_ptr()), N, int(samples),
+                                     ctypes.c_uint64(seed & (2 ** 64 - 1)), _dtype_code(psi),
+                                     ctypes.byref(M), ctypes.byref(se), _stream(psi)), "hadamag_sre_mc")
     return M.value, se.value
 
 

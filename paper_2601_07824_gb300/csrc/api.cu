@@ -343,7 +343,7 @@ hadamag_status sre_sums(hadamag_ctx_t c, const float2* p, int N, double n, cudaS
     const int64_t dim = int64_t(1) << N;
     bool tensor = use_tensor_path(c, N, n);
     if (tensor) {
-        if ((s = run_sre_tensor(c, p, N, n, st, &nparts))) return s;
+        if ((s = run_sre_tensor(c, p, N, n, dim, nullptr, 0, nullptr, st, &nparts))) return s;
     } else {
         if ((s = run_sre(c, p, N, n, dim, nullptr, 0, nullptr, st, &nparts))) return s;
     }
@@ -403,7 +403,8 @@ extern "C" hadamag_status hadamag_sre_terms(hadamag_ctx_t c, const void* psi, in
     if (count == 0) return finish(c, nullptr, 0, st);
     const float2* p;
     if ((s = as_c64(c, psi, int64_t(1) << N, dt, st, &p))) return s;
-    if (N <= 24) s = run_sre(c, p, N, n, count, a_list, 1, terms, st, nullptr);
+    if (use_tensor_path(c, N, n)) s = run_sre_tensor(c, p, N, n, count, a_list, 1, terms, st, nullptr);
+    else if (N <= 24) s = run_sre(c, p, N, n, count, a_list, 1, terms, st, nullptr);
     else s = run_sre_hbm_terms(c, p, N, count, a_list, terms, st);
     if (s) return s;
     return finish(c, nullptr, 0, st);
@@ -442,7 +443,8 @@ extern "C" hadamag_status hadamag_sre_mc(hadamag_ctx_t c, const void* psi, int N
     c->launches++;
     if (e != cudaSuccess) return cuda_fail(c, e, "mc_xstrings");
     if ((e = cudaMemsetAsync(al + samples, 0, sizeof(int64_t), st)) != cudaSuccess) return cuda_fail(c, e, "memset");
-    if (N <= 24) s = run_sre(c, p, N, 2.0, samples + 1, al, 1, tm, st, nullptr);
+    if (use_tensor_path(c, N, 2.0)) s = run_sre_tensor(c, p, N, 2.0, samples + 1, al, 1, tm, st, nullptr);
+    else if (N <= 24) s = run_sre(c, p, N, 2.0, samples + 1, al, 1, tm, st, nullptr);
     else s = run_sre_hbm_terms(c, p, N, samples + 1, al, tm, st);
     if (s) return s;
     e = launch_mc_stats(tm, al, samples, (double*)c->res.ptr, st);
