@@ -6,7 +6,7 @@ Default workload (one step = one complete exact M_2 of one state, every X-string
   FP32 CUDA-core Walsh-Hadamard path, 4^20 = 1.1e12 Pauli strings per step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--N 20] [--path cudacore|tensor] [--no-cpu-baseline] [--extra]
+                  [--N 20] [--path cudacore|tensor] [--no-cpu-baseline] [--extra] [--xstrings K]
 
 Multi-GPU (torchrun, one rank per GPU): the X-strings are independent (Sec. 3.1.2), so every
 rank runs the same per-state work on its own replica ("scaling": "weak", no collective on
@@ -42,6 +42,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--extra", action="store_true", help="also time N=22, mana N=11, MC N=28, batched")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--xstrings", type=int, default=0,
+                    help="profiling aid: each step evaluates only the first K X-strings of the "
+                         "workload (per-X-string sums) instead of the full M_2")
     return ap.parse_args()
 
 
@@ -63,6 +66,25 @@ def ops_per_string(N: int) -> int:
 
 def fp32_peak_ops(sm_count: int, mhz: float) -> float:
     return sm_count * 128 * mhz * 1e6
+
+
+def tensor_flops_per_string(N: int) -> int:
+    # tensor-core path: each Pauli string is one real value of the half-length transform; its
+    # Kronecker blocks are K = 128, 64 and 128 wide (pass 1: 7 + 6 bits, pass 2: 7 bits), each
+    # applied to the hi and the lo operand: 2 (hi, lo) x 2 (multiply-add) x (128 + 64 + 128)
+    return 4 * (128 + 64 + 128)
+
+
+def measured_peak(key: str, fallback: float):
+    """A peak from MEASURED_PEAKS.json (driver-written) and where it came from."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            v = json.load(f).get(key)
+        if v:
+            return float(v), "measured"
+    except (OSError, ValueError):
+        pass
+    return fallback, "fallback"
 
 
 class ClockSampler:
@@ -230,9 +252,14 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
 
-    M = None
+    M = ln = None
+    if args.xstrings > 0:
+        alist = torch.arange(args.xstrings, dtype=torch.int64, device=dev)
+        step = lambda: (hm.sre_terms(psi, 2.0, alist), None)  # noqa: E731
+    else:
+        step = lambda: hm.sre(psi, 2.0)  # noqa: E731
     for _ in range(args.warmup):
-        M, ln = hm.sre(psi, 2.0)
+        M, ln = step()
     barrier()
     launches0 = ctx.launch_count()
     ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
@@ -241,7 +268,7 @@ def main():
         for s in range(args.steps):
             flush.fill_(s & 0xFF)  # evict L2 between steps (the state is smaller than L2)
             ev[s][0].record(stream)
-            M, ln = hm.sre(psi, 2.0)
+            M, ln = step()
             ev[s][1].record(stream)
         barrier()
     launches = ctx.launch_count() - launches0
@@ -251,13 +278,15 @@ def main():
     if world > 1:
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
     t_max = float(t.item())
-    strings_per_step = 4.0 ** N
+    strings_per_step = 4.0 ** N if args.xstrings <= 0 else float(args.xstrings) * 2 ** N
+    if args.xstrings > 0:
+        M = ln = None
     value = world * args.steps * strings_per_step / t_max
     clocks = clk.summary()
 
     # end-to-end: the C-ABI host-buffer call, H2D copy from pinned memory inside the timed region
     e2e = None
-    if not args.no_e2e:
+    if not args.no_e2e and args.xstrings <= 0:
         host = torch.from_numpy(psi_np).pin_memory()
         hm.sre_host(host.numpy(), 2.0, device=local)
         barrier()
@@ -273,29 +302,41 @@ def main():
 
     line = None
     if rank == 0:
-        ops = ops_per_string(N) * strings_per_step
         avg_s = t_local / args.steps
-        achieved = ops / avg_s
         mhz_max = 2070.0
-        peak = fp32_peak_ops(sm_count, mhz_max)
+        if args.path == "tensor" and 21 <= N <= 24:
+            # tensor-core path (21 <= N <= 24): tensor-pipe FLOPs against the measured dense
+            # fp16/bf16 peak (same rate for both types); smaller N runs the CUDA-core kernels
+            peak, src = measured_peak("bf16_tflops", 1900.0)
+            peak *= 1e12
+            achieved = tensor_flops_per_string(N) * strings_per_step / avg_s
+            roof = {"bound": "tensor", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "note": f"{tensor_flops_per_string(N)} fp16 tensor FLOPs per Pauli string (blocks of K = "
+                            f"128, 64, 128 on hi and lo operands); peak = {src} dense bf16 burst"}
+        else:
+            achieved = ops_per_string(N) * strings_per_step / avg_s
+            peak = fp32_peak_ops(sm_count, mhz_max)
+            roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
+                    "frac": achieved / peak, "traffic": None,
+                    "note": f"FP32 ops (FMA = 1) = {ops_per_string(N)} per Pauli string; peak = "
+                            f"{sm_count} SMs x 128 lanes x {mhz_max:.0f} MHz; kernel time = CUDA events "
+                            "around the call on its stream"}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-            "config": {"workload": f"exact M2, N={N}: {desc}; complex64; FP32 {args.path} Walsh-Hadamard path",
+            "config": {"workload": (f"exact M2, N={N}: {desc}; complex64; {args.path} Walsh-Hadamard path"
+                                    + (f"; first {args.xstrings} X-strings only (profiling)" if args.xstrings > 0 else "")),
                        "N": N, "n": 2, "strings_per_step": strings_per_step,
-                       "l2": "state (8 MiB) is smaller than L2: a 256 MiB buffer is written between steps",
+                       "l2": f"state ({psi_np.nbytes >> 20} MiB) is smaller than L2: a 256 MiB buffer is written between steps",
                        "M2": M, "lost_norm": ln},
-            "roofline": {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
-                         "note": f"FP32 ops (FMA = 1) = {ops_per_string(N)} per Pauli string; peak = "
-                                 f"{sm_count} SMs x 128 lanes x {mhz_max:.0f} MHz; kernel time = CUDA events "
-                                 "around the call on its stream"},
+            "roofline": roof,
             "clocks": clocks,
             "gpu_launches": launches,
             "e2e": e2e,
         }
-        if clocks.get("sm_mhz"):
+        if clocks.get("sm_mhz") and roof["bound"] == "alu":
             line["roofline"]["frac_at_measured_clock"] = achieved / fp32_peak_ops(sm_count, clocks["sm_mhz"])
     if world > 1:
         dist.barrier()
@@ -311,14 +352,15 @@ def main():
 
 
 def extra_workloads(hm, dev, sm_count):
-    """Other configurations, one timed call each (not part of the headline value)."""
+    """The other configurations, one timed call each (not part of the headline value)."""
     import numpy as np
     import torch
     from paper_2601_07824_gb300 import _lib, inputs
     out = {}
 
-    def timed(fn, reps=1):
-        fn()
+    def timed(fn, reps=1, warm=True):
+        if warm:
+            fn()
         torch.cuda.synchronize(dev)
         t0 = time.perf_counter()
         for _ in range(reps):
@@ -326,22 +368,57 @@ def extra_workloads(hm, dev, sm_count):
         torch.cuda.synchronize(dev)
         return (time.perf_counter() - t0) / reps, r
 
-    ctx = _lib.context(dev.index or 0)
-    psi22 = torch.from_numpy(inputs.gaussian_state(22, 2201, dtype=np.complex64)).to(dev)
-    for name, p in (("cudacore", _lib.PATH_CUDACORE), ("tensor", _lib.PATH_TENSOR)):
+    def guard(key, fn):
         try:
-            ctx.set_path(p)
-            dt, r = timed(lambda: hm.sre(psi22, 2.0))
-            out[f"sre_N22_{name}"] = {"strings_per_s": 4.0 ** 22 / dt, "s": dt, "M2": r[0]}
+            out[key] = fn()
         except Exception as e:  # noqa: BLE001
-            out[f"sre_N22_{name}"] = {"error": str(e)}
-    ctx.set_path(_lib.PATH_CUDACORE)
-    try:
+            out[key] = {"error": str(e)}
+
+    tpeak, tsrc = measured_peak("bf16_tflops_sustained", 1700.0)
+
+    # exact M2 at N = 22 (Gaussian state): FP32 CUDA-core path vs tensor-core path
+    psi22 = torch.from_numpy(inputs.gaussian_state(22, 2201, dtype=np.complex64)).to(dev)
+    res = {}
+    for name, p in (("cudacore", _lib.PATH_CUDACORE), ("tensor", _lib.PATH_TENSOR)):
+        def run22(p=p, name=name):
+            dt, r = timed(lambda: hm.sre(psi22, 2.0, path=p), warm=False)
+            rate = 4.0 ** 22 / dt
+            d = {"strings_per_s": rate, "s": dt, "M2": r[0], "lost_norm": r[1]}
+            if name == "tensor":
+                d["tensor_frac_of_sustained_peak"] = tensor_flops_per_string(22) * rate / (tpeak * 1e12)
+                d["peak_source"] = tsrc
+            else:
+                d["alu_frac"] = ops_per_string(22) * rate / fp32_peak_ops(sm_count, 2070.0)
+            res[name] = d
+            return d
+        guard(f"sre_N22_{name}", run22)
+    if "cudacore" in res and "tensor" in res:
+        out["sre_N22_tensor_over_cudacore"] = res["tensor"]["strings_per_s"] / res["cudacore"]["strings_per_s"]
+        out["sre_N22_rel_dM2"] = abs(res["tensor"]["M2"] - res["cudacore"]["M2"]) / res["cudacore"]["M2"]
+    del psi22
+
+    # exact mana of an N = 11 qutrit Gaussian state
+    def mana11():
         q = torch.from_numpy(inputs.gaussian_state(11, 1101, d=3, dtype=np.complex64)).to(dev)
-        dt, r = timed(lambda: hm.mana(q), reps=5)
-        out["mana_N11"] = {"points_per_s": 9.0 ** 11 / dt, "s": dt, "mana": r[0]}
-    except Exception as e:  # noqa: BLE001
-        out["mana_N11"] = {"error": str(e)}
+        dt, r = timed(lambda: hm.mana(q), reps=3)
+        return {"points_per_s": 9.0 ** 11 / dt, "s": dt, "mana": r[0]}
+    guard("mana_N11", mana11)
+
+    # Monte-Carlo M2 at N = 28 with 4096 sampled X-strings (plus the exact a = 0 row)
+    def mc28():
+        psi = torch.from_numpy(inputs.gaussian_state(28, 2801, dtype=np.complex64)).to(dev)
+        dt, r = timed(lambda: hm.sre_mc(psi, 4096, 2802), warm=False)
+        return {"strings_per_s": 4097 * 2.0 ** 28 / dt, "s": dt, "M2": r[0], "stderr": r[1],
+                "hbm_state_reads_GBps": 4097 * 2 * psi.numel() * 8 / dt / 1e9}
+    guard("mc_N28", mc28)
+
+    # batched forward + backward: 64 states, N uniform in 10..18, one persistent launch
+    def batched():
+        Ns, states = inputs.batched_ladder_states(64, 10, 18, 8, seed=4001)
+        ts = [torch.from_numpy(x).to(dev) for x in states]
+        dt, _ = timed(lambda: hm.sre_batched(ts, want_grad=True), reps=2)
+        return {"strings_per_s": sum(4.0 ** n for n in Ns) / dt, "s": dt, "states": len(Ns)}
+    guard("batched_64_fwd_bwd", batched)
     return out
 
 

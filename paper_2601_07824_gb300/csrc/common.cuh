@@ -137,24 +137,36 @@ __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_gr
 //   s1 = Re^2 + Im^2         (scaled by 4)
 //   u  = Re^2 log2 Re^2 + Im^2 log2 Im^2   (n = 1 only)
 // MODE 1: n = 1, 2: n = 2, 3: n = 3, 0: any n > 0 (q accumulated in FP64 from exp2(n log2)).
+// The integer-n sums run as two interleaved FP32 lanes (packed FADD2/FFMA2); `q` and `s1`
+// are valid after fold().
 template <int MODE>
 struct Acc {
     float q = 0.f, s1 = 0.f, u = 0.f;
     double qd = 0.0;
+    float2 qv = make_float2(0.f, 0.f), sv = make_float2(0.f, 0.f);
     __device__ __forceinline__ void add(float2 w, double nq) {
         float2 sq = mul2(w, w);
-        s1 += sq.x + sq.y;
         if constexpr (MODE == 2) {
-            float2 f = mul2(sq, sq);
-            q += f.x + f.y;
+            sv = add2(sv, sq);
+            qv = fma2(sq, sq, qv);
+            return;
         } else if constexpr (MODE == 3) {
-            float2 f = mul2(mul2(sq, sq), sq);
-            q += f.x + f.y;
-        } else if constexpr (MODE == 1) {
+            sv = add2(sv, sq);
+            qv = fma2(mul2(sq, sq), sq, qv);
+            return;
+        }
+        s1 += sq.x + sq.y;
+        if constexpr (MODE == 1) {
             u += (sq.x > 0.f ? sq.x * log2f(sq.x) : 0.f) + (sq.y > 0.f ? sq.y * log2f(sq.y) : 0.f);
         } else {
             double px = 4.0 * (double)sq.x, py = 4.0 * (double)sq.y;
             qd += (px > 0.0 ? exp2(nq * log2(px)) : 0.0) + (py > 0.0 ? exp2(nq * log2(py)) : 0.0);
+        }
+    }
+    __device__ __forceinline__ void fold() {
+        if constexpr (MODE == 2 || MODE == 3) {
+            q = qv.x + qv.y;
+            s1 = sv.x + sv.y;
         }
     }
 };

@@ -60,6 +60,7 @@ sre_onepass(const float2* __restrict__ psi, int N, double nq, int64_t count,
         Acc<MODE> ac;
 #pragma unroll
         for (int i = 0; i < (1 << E); ++i) ac.add(x[i], nq);
+        ac.fold();
         float q = ac.q, s1 = ac.s1, u = ac.u;
         double qd = ac.qd;
         double v[3];
@@ -245,6 +246,7 @@ __global__ void __launch_bounds__(256, 2) sre_twopass(TwoPassParams P) {
                 Acc<MODE> ac;
 #pragma unroll
                 for (int k = 0; k < 32; ++k) ac.add(x[k], P.nq);
+                ac.fold();
                 float q = ac.q, s1 = ac.s1, u = ac.u;
                 double qd = ac.qd;
                 warp_sum3<MODE>(q, s1, u, qd, 32);

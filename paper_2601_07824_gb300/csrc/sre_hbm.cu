@@ -112,6 +112,7 @@ __global__ void __launch_bounds__(256, 2) sre_threepass(HbmParams P) {
                 Acc<2> ac;
 #pragma unroll
                 for (int k = 0; k < 32; ++k) ac.add(x[k], 2.0);
+                ac.fold();
                 float q = ac.q, s1 = ac.s1, u = 0.f;
                 double qd = 0.0;
                 warp_sum3<2>(q, s1, u, qd, 32);

@@ -429,7 +429,12 @@ __global__ void __launch_bounds__(256, 1) sre_tc(TcParams P) {
             tc::fence_before();
             Acc<MODE> ac;
 #pragma unroll
-            for (int k = 0; k < 32; ++k) ac.add(mul2(make_float2(v[2 * k], v[2 * k + 1]), make_float2(RSF, RSF)), P.nq);
+            for (int k = 0; k < 32; ++k) {
+                float2 w = make_float2(v[2 * k], v[2 * k + 1]);
+                if constexpr (RS != 0) w = mul2(w, make_float2(RSF, RSF));
+                ac.add(w, P.nq);
+            }
+            ac.fold();
             float q = ac.q, s1 = ac.s1, uu = ac.u;
             double qd = ac.qd;
             warp_sum3<MODE>(q, s1, uu, qd, 32);

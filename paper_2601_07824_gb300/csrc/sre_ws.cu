@@ -156,6 +156,7 @@ __global__ void __launch_bounds__(512, 1) sre_ws(WsParams P) {
             Acc<MODE> ac;
 #pragma unroll
             for (int k = 0; k < 32; ++k) ac.add(x[k], P.nq);
+            ac.fold();
             float q = ac.q, s1 = ac.s1, u = ac.u;
             double qd = ac.qd;
             warp_sum3<MODE>(q, s1, u, qd, 32);

@@ -49,14 +49,17 @@ __device__ __forceinline__ void mbar_init(uint64_t* mbar, uint32_t count) {
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
 }
 
-// Bounded wait for the phase with parity `parity` of `mbar` to complete.
+// Bounded wait for the phase with parity `parity` of `mbar` to complete.  Each try_wait
+// suspends the thread (no issue slots) until the phase completes or 100 us pass; the loop
+// gives up after limit / 1024 (at least 16) such periods.
 __device__ __forceinline__ bool mbar_wait(uint64_t* mbar, uint32_t parity, long long limit) {
-    for (long long it = 0; it < limit; ++it) {
+    const long long n = (limit >> 10) < 16 ? 16 : (limit >> 10);
+    for (long long it = 0; it < n; ++it) {
         uint32_t ok;
         asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}"
             : "=r"(ok)
-            : "r"(smem_u32(mbar)), "r"(parity)
+            : "r"(smem_u32(mbar)), "r"(parity), "r"(100000u)
             : "memory");
         if (ok) return true;
     }

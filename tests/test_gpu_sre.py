@@ -74,11 +74,11 @@ def test_per_x_terms_vs_oracle(N):
     at = torch.from_numpy(a.astype(np.int64)).to(DEV)
     for n in (1.0, 2.0, 3.0):
         got = hm.sre_terms(on_dev(psi), n, at).cpu().numpy()
-        Sq, S1, T1 = oracle.sre_terms(psi, n, 0, dim)
-        np.testing.assert_allclose(got[:, 0], Sq[a], rtol=2e-5)
-        np.testing.assert_allclose(got[:, 1], S1[a], rtol=2e-5)
+        want = np.array([[v[0] for v in oracle.sre_terms(psi, n, int(ai), int(ai) + 1)] for ai in a])
+        np.testing.assert_allclose(got[:, 0], want[:, 0], rtol=2e-5)
+        np.testing.assert_allclose(got[:, 1], want[:, 1], rtol=2e-5)
         if n == 1.0:
-            np.testing.assert_allclose(got[:, 2], T1[a], rtol=2e-5, atol=1e-7 * np.abs(T1).max())
+            np.testing.assert_allclose(got[:, 2], want[:, 2], rtol=2e-5, atol=1e-7 * np.abs(want[:, 2]).max())
 
 
 def test_twopass_full_vs_oracle_N16():
@@ -105,7 +105,7 @@ def test_twopass_sampled_terms_and_exact_identities(N):
     z = np.arange(dim)
     s1 = np.array([dim * np.sum(p * p[z ^ ai]) for ai in a])
     np.testing.assert_allclose(got[:, 1], s1, rtol=2e-5)
-    if N <= 22:
+    if N <= 20:
         M, ln = hm.sre(t, 2.0)
         # lost_norm = 1 - |psi|^4 exactly (Eq. distNAT), at any N
         assert abs(ln - (1.0 - np.sum(p) ** 2)) < 1e-6
