@@ -16,7 +16,7 @@
 
 namespace hm {
 
-template <int L>
+template <int L, bool FWD>
 __device__ __forceinline__ void small_item(const BatchState& s, float2* smem, double* m2_out, int idx) {
     constexpr int G = OnepassShape<L>::G, GPC = 256 / G;  // groups of one 256-thread CTA
     static_assert(L >= 9 && L <= 13, "small items cover N = 10..14");
@@ -25,13 +25,13 @@ __device__ __forceinline__ void small_item(const BatchState& s, float2* smem, do
     const int64_t dim = int64_t(1) << L << 1;
     float2* sm = smem + (size_t)gi * tile_slots(L);
     double acc = 0.0, acc1 = 0.0;
-    grad_onepass_group<L>(s.psi, L + 1, s.gsmall + (size_t)gi * dim, gi, GPC, sm, acc, acc1);
+    grad_onepass_group<L, FWD>(s.psi, L + 1, FWD ? nullptr : s.gsmall + (size_t)gi * dim, gi, GPC, sm, acc, acc1);
     if (t == 0) { sums[gi][0] = acc; sums[gi][1] = acc1; }
     __syncthreads();
     double S2 = 0.0;
     for (int k = 0; k < GPC; ++k) S2 += sums[k][0];
     const double scale = -1.0 / (0.69314718055994530942 * S2);
-    for (int64_t z = tid; z < dim; z += blockDim.x) {
+    if (!FWD) for (int64_t z = tid; z < dim; z += blockDim.x) {
         double gx = 0.0, gy = 0.0;
         for (int k = 0; k < GPC; ++k) {
             const float2 v = s.gsmall[(size_t)k * dim + z];
@@ -45,7 +45,27 @@ __device__ __forceinline__ void small_item(const BatchState& s, float2* smem, do
 }
 
 template <int M>
+__device__ __forceinline__ bool large_task_fwd(const BatchState& s, const G3Ctl& ctl, int64_t local, float2* smem) {
+    // forward only: stage st = pass 1 of batch st, pass 2 of batch st - 1; a slot is reused once
+    // its pass 2 is done (the done3 / p3 fields of the state view point at done2 / p2)
+    const G3State S{s.psi, s.N, s.scratch, s.R, s.A, s.U, s.n_batches, s.p1, s.p2, s.p2,
+                    s.ctr, s.ctr + 64, s.ctr + 64};
+    const int64_t per_stage = (int64_t)s.p1 + s.p2;
+    const int64_t st = local / per_stage;
+    int r = (int)(local % per_stage);
+    if (r < s.p1) {
+        if (st >= s.n_batches) return true;
+        return g3_pass1<M>(S, ctl, st, r, smem);
+    }
+    r -= s.p1;
+    if (st - 1 < 0 || st - 1 >= s.n_batches) return true;
+    double acc = 0.0, acc1 = 0.0;
+    return g3_pass2<M, true>(S, ctl, st - 1, r, smem, acc, acc1, s.s2);
+}
+
+template <int M>
 __device__ __forceinline__ bool large_task(const BatchedParams& B, const BatchState& s, int64_t local, float2* smem) {
+    if (s.fwd) return large_task_fwd<M>(s, B.ctl, local, smem);
     const G3State S{s.psi, s.N, s.scratch, s.R, s.A, s.U, s.n_batches, s.p1, s.p2, s.p3,
                     s.ctr, s.ctr + 64, s.ctr + 128};
     const int64_t per_stage = (int64_t)s.p1 + s.p2 + s.p3;
@@ -69,6 +89,20 @@ __device__ __forceinline__ bool large_task(const BatchedParams& B, const BatchSt
 
 __device__ __forceinline__ bool finalize_task(const BatchedParams& B, const BatchState& s, int f, double* m2_out,
                                               int idx) {
+    if (s.fwd) {
+        // forward only: every pass-2 task has added its sums into s2
+        for (int k = 0; k < s.R; ++k) {
+            const int64_t nb = (s.n_batches > k) ? (s.n_batches - k + s.R - 1) / s.R : 0;
+            if (!cta_wait_geq(s.ctr + 64 + k, (unsigned)(nb * s.p2) + B.ctl.wait_bias, B.ctl.status, B.ctl.spin_limit))
+                return false;
+        }
+        if (threadIdx.x == 0) {
+            const double S2 = *reinterpret_cast<volatile double*>(s.s2);
+            m2_out[s.out_idx] = -log2(S2 / (double)(int64_t(1) << s.N));
+        }
+        __syncthreads();
+        return true;
+    }
     // all pass-3 tasks of this state are done: every slot's counter reached its final value
     for (int k = 0; k < s.R; ++k) {
         const int64_t nb = (s.n_batches > k) ? (s.n_batches - k + s.R - 1) / s.R : 0;
@@ -113,12 +147,17 @@ __global__ void __launch_bounds__(256, 2) batched_kernel(BatchedParams B) {
         const int64_t local = tau - s.task_begin;
         bool ok = true;
         if (s.kind == 0) {
-            switch (s.N) {
-                case 10: small_item<9>(s, smem, B.m2_out, idx); break;
-                case 11: small_item<10>(s, smem, B.m2_out, idx); break;
-                case 12: small_item<11>(s, smem, B.m2_out, idx); break;
-                case 13: small_item<12>(s, smem, B.m2_out, idx); break;
-                case 14: small_item<13>(s, smem, B.m2_out, idx); break;
+            switch (s.N * 2 + s.fwd) {
+                case 20: small_item<9, false>(s, smem, B.m2_out, idx); break;
+                case 22: small_item<10, false>(s, smem, B.m2_out, idx); break;
+                case 24: small_item<11, false>(s, smem, B.m2_out, idx); break;
+                case 26: small_item<12, false>(s, smem, B.m2_out, idx); break;
+                case 28: small_item<13, false>(s, smem, B.m2_out, idx); break;
+                case 21: small_item<9, true>(s, smem, B.m2_out, idx); break;
+                case 23: small_item<10, true>(s, smem, B.m2_out, idx); break;
+                case 25: small_item<11, true>(s, smem, B.m2_out, idx); break;
+                case 27: small_item<12, true>(s, smem, B.m2_out, idx); break;
+                case 29: small_item<13, true>(s, smem, B.m2_out, idx); break;
                 default: break;
             }
         } else if (local < s.n_stage_tasks) {

@@ -12,6 +12,7 @@ struct BatchState {
     float2* grad;              // dM_2/dpsi* out (complex64) or null
     int N;
     int kind;                  // 0: small (one CTA item), 1: large (three passes + finalize)
+    int fwd;                   // 1: M_2 only (large: two passes + one finalize task)
     int out_idx;               // position of this state in the caller's arrays
     int64_t task_begin;        // first ticket of this state's segment
     // small states
@@ -21,7 +22,7 @@ struct BatchState {
     int R, A, U;
     int64_t n_batches;
     int p1, p2, p3;
-    int64_t n_stage_tasks;     // (n_batches + 2) * (p1 + p2 + p3)
+    int64_t n_stage_tasks;     // (n_batches + 2) * (p1 + p2 + p3); forward: (n_batches + 1) * (p1 + p2)
     int n_fin;                 // finalize tasks
     unsigned* ctr;             // [64 done1][64 done2][64 done3], zeroed before launch
     unsigned* fin;             // finalize tasks done (zeroed)

@@ -26,7 +26,7 @@ struct Plan {
 };
 
 // Builds the state table (offsets into the context buffers are filled in later).
-Plan make_plan(int count, const void* const* psi, const int* N, void* const* grad, int A_large) {
+Plan make_plan(int count, const void* const* psi, const int* N, void* const* grad, int A_large, bool fwd) {
     std::vector<int> order(count);
     for (int i = 0; i < count; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
@@ -42,10 +42,11 @@ Plan make_plan(int count, const void* const* psi, const int* N, void* const* gra
         s.N = N[i];
         s.task_begin = p.total;
         s.out_idx = i;
+        s.fwd = fwd ? 1 : 0;
         const int64_t dim = int64_t(1) << s.N;
         if (s.N <= 14) {
             s.kind = 0;
-            p.gsmall_bytes += (size_t)(256 / (1 << (s.N - 6))) * dim * sizeof(float2);
+            if (!fwd) p.gsmall_bytes += (size_t)(256 / (1 << (s.N - 6))) * dim * sizeof(float2);
             p.total += 1;
         } else {
             s.kind = 1;
@@ -57,8 +58,13 @@ Plan make_plan(int count, const void* const* psi, const int* N, void* const* gra
             s.p1 = (1 << M) / (s.U * 2);
             s.p2 = s.A * (1024 >> (13 - M));
             s.p3 = s.A * ((1 << M) / 16);
-            s.n_stage_tasks = (s.n_batches + 2) * ((int64_t)s.p1 + s.p2 + s.p3);
-            s.n_fin = (int)std::max<int64_t>(1, dim / 2048);
+            if (fwd) {
+                s.n_stage_tasks = (s.n_batches + 1) * ((int64_t)s.p1 + s.p2);
+                s.n_fin = 1;
+            } else {
+                s.n_stage_tasks = (s.n_batches + 2) * ((int64_t)s.p1 + s.p2 + s.p3);
+                s.n_fin = (int)std::max<int64_t>(1, dim / 2048);
+            }
             p.scratch_bytes += (size_t)s.R * s.A * (size_t)(dim / 2) * sizeof(float2);
             p.total += s.n_stage_tasks + s.n_fin;
             p.n_large++;
@@ -90,7 +96,7 @@ hadamag_status run(hadamag_ctx_t c, int count, const void* const* psi, const int
                    void* const* grad, double* m2, cudaStream_t st, int A_large) {
     hadamag_status s;
     cudaError_t e;
-    Plan p = make_plan(count, psi, N, want_grad ? grad : nullptr, A_large);
+    Plan p = make_plan(count, psi, N, want_grad ? grad : nullptr, A_large, !want_grad);
     const int ns = (int)p.st.size();
     int grid = 0;
     if ((e = batched_max_grid(c->sm_count, &grid)) != cudaSuccess) return cuda_fail(c, e, "occupancy");
@@ -102,7 +108,7 @@ hadamag_status run(hadamag_ctx_t c, int count, const void* const* psi, const int
     if ((s = ensure_buf(c, c->batch_meta, meta_bytes))) return s;
     if ((s = ensure_buf(c, c->scratch, std::max<size_t>(p.scratch_bytes, 256)))) return s;
     if ((s = ensure_buf(c, c->batch_sums, std::max<size_t>(p.gsmall_bytes, 256)))) return s;
-    const size_t gpart_bytes = p.n_large ? (size_t)grid * p.dimmax * sizeof(float2) : 256;
+    const size_t gpart_bytes = (p.n_large && want_grad) ? (size_t)grid * p.dimmax * sizeof(float2) : 256;
     if ((s = ensure_buf(c, c->grad_acc, gpart_bytes))) return s;
     if (c->host_table_bytes < table_bytes) {
         if (c->host_table) cudaFreeHost(c->host_table);
@@ -124,8 +130,10 @@ hadamag_status run(hadamag_ctx_t c, int count, const void* const* psi, const int
         b.fin = b.ctr + 192;
         b.s2 = s2 + 2 * k;
         if (b.kind == 0) {
-            b.gsmall = (float2*)((char*)c->batch_sums.ptr + goff);
-            goff += (size_t)(256 / (1 << (b.N - 6))) * ((size_t)1 << b.N) * sizeof(float2);
+            if (want_grad) {
+                b.gsmall = (float2*)((char*)c->batch_sums.ptr + goff);
+                goff += (size_t)(256 / (1 << (b.N - 6))) * ((size_t)1 << b.N) * sizeof(float2);
+            }
         } else {
             b.scratch = (float2*)((char*)c->scratch.ptr + soff);
             soff += (size_t)b.R * b.A * ((size_t)1 << (b.N - 1)) * sizeof(float2);
@@ -141,7 +149,7 @@ hadamag_status run(hadamag_ctx_t c, int count, const void* const* psi, const int
     if ((e = cudaMemsetAsync(ctr, 0, ctr_bytes + s2_bytes + 256, st)) != cudaSuccess) return cuda_fail(c, e, "memset");
     if (p.gsmall_bytes && (e = cudaMemsetAsync(c->batch_sums.ptr, 0, p.gsmall_bytes, st)) != cudaSuccess)
         return cuda_fail(c, e, "memset");
-    if (p.n_large && (e = cudaMemsetAsync(c->grad_acc.ptr, 0, gpart_bytes, st)) != cudaSuccess)
+    if (p.n_large && want_grad && (e = cudaMemsetAsync(c->grad_acc.ptr, 0, gpart_bytes, st)) != cudaSuccess)
         return cuda_fail(c, e, "memset");
     BatchedParams B{};
     B.states = (const BatchState*)meta;

@@ -89,7 +89,8 @@ __device__ __forceinline__ bool g3_pass1(const G3State& S, const G3Ctl& C, int64
 
 // ---- pass 2: tile r of batch g; adds 16 sum(R^4+I^4) and 4 sum(R^2+I^2) into acc/acc1 (thread 0)
 // If s2_atomic is given, thread 0 also adds this task's two sums to it before the task's release.
-template <int M>
+// FWD: forward only (M_2 without the gradient): no cube, back-transform or store.
+template <int M, bool FWD = false>
 __device__ __forceinline__ bool g3_pass2(const G3State& S, const G3Ctl& C, int64_t g, int r, float2* smem,
                                          double& acc, double& acc1, double* s2_atomic = nullptr) {
     constexpr int K1 = 10, L = K1 + M, LOGT = 13 - M, T = 1 << LOGT, TILES = 1024 / T;
@@ -122,6 +123,7 @@ __device__ __forceinline__ bool g3_pass2(const G3State& S, const G3Ctl& C, int64
             q = fmaf(sq.x, sq.x, fmaf(sq.y, sq.y, q));
             x[k] = cube_parts(x[k]);
         }
+        if constexpr (!FWD) {
         // back to the round-0 layout, transform the high bits again, store in place
         __syncthreads();
 #pragma unroll
@@ -135,6 +137,7 @@ __device__ __forceinline__ bool g3_pass2(const G3State& S, const G3Ctl& C, int64
         for (int k = 0; k < 32; ++k) {
             const uint32_t j = deposit<5>(tid, k, SL2);
             __stcg(src + ((size_t)(j >> LOGT) << K1) + (j & (T - 1)), x[k]);
+        }
         }
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) { q += __shfl_xor_sync(0xffffffffu, q, o); s1 += __shfl_xor_sync(0xffffffffu, s1, o); }
@@ -208,8 +211,8 @@ __device__ __forceinline__ bool g3_pass3(const G3State& S, const G3Ctl& C, int64
 
 // One-pass adjoint of a whole state by one group of threads (see grad.cu): X-strings
 // a = gg, gg + ngroups, ...; contributions go to gp (this group's partial, 2^N values);
-// the group leader (t == 0) receives the group's S_2 and S_1 sums.
-template <int L>
+// the group leader (t == 0) receives the group's S_2 and S_1 sums.  FWD: the sums only.
+template <int L, bool FWD = false>
 __device__ __forceinline__ void grad_onepass_group(const float2* __restrict__ psi, int N, float2* __restrict__ gp,
                                                    int64_t gg, int64_t ngroups, float2* sm, double& acc,
                                                    double& acc1) {
@@ -240,6 +243,7 @@ __device__ __forceinline__ void grad_onepass_group(const float2* __restrict__ ps
             q = fmaf(sq.x, sq.x, fmaf(sq.y, sq.y, q));
             x[i] = cube_parts(x[i]);
         }
+        if constexpr (!FWD) {
         if constexpr (L >= 5) {
             if constexpr (G <= 32) __syncwarp(); else __syncthreads();
 #pragma unroll
@@ -262,6 +266,7 @@ __device__ __forceinline__ void grad_onepass_group(const float2* __restrict__ ps
                     scatter_zero(gp, psi, zp << 1, x[i]);
                 }
             }
+        }
         }
         if constexpr (G <= 32) {
 #pragma unroll
