@@ -105,11 +105,27 @@ __device__ __forceinline__ void produce_near(const float2* __restrict__ psi, con
 // All threads wait for phase `ph` of `mbar`; uniform result.  On a timeout the status word is
 // set and the threads that gave up wait once more (bounded) so that outstanding asynchronous
 // work drains before the caller frees its resources.
-__device__ __forceinline__ bool wait_bar(uint64_t* mbar, uint32_t& ph, int* status, long long limit) {
+// The CTA runs two independent groups of 256 threads (warps 0-7: pass 1, warps 8-15:
+// pass 2); each synchronises on its own named barrier (id 1 + group).
+__device__ __forceinline__ void gsync(int id) { asm volatile("bar.sync %0, 256;" ::"r"(id) : "memory"); }
+__device__ __forceinline__ int gsync_or(int id, int pred) {
+    int r;
+    asm volatile(
+        "{\n .reg .pred p, q;\n setp.ne.b32 p, %2, 0;\n bar.red.or.pred q, %1, 256, p;\n selp.s32 %0, 1, 0, q;\n}"
+        : "=r"(r)
+        : "r"(id), "r"(pred)
+        : "memory");
+    return r;
+}
+
+// All threads of a group wait for phase `ph` of `mbar`; uniform result.  On a timeout the
+// status word is set and the threads that gave up wait once more (bounded) so that
+// outstanding asynchronous work drains before the caller frees its resources.
+__device__ __forceinline__ bool wait_bar(uint64_t* mbar, uint32_t& ph, int* status, long long limit, int id) {
     const bool good = tc::mbar_wait(mbar, ph, limit);
-    const int bad = __syncthreads_or(!good);
+    const int bad = gsync_or(id, !good);
     if (bad) {
-        if (threadIdx.x == 0) atomicOr(status, ST_TIMEOUT);
+        if ((threadIdx.x & 255u) == 0) atomicOr(status, ST_TIMEOUT);
         if (!good) tc::mbar_wait(mbar, ph, limit);
     }
     ph ^= 1u;
@@ -117,12 +133,32 @@ __device__ __forceinline__ bool wait_bar(uint64_t* mbar, uint32_t& ph, int* stat
     return !bad;
 }
 
-// Operand writes (generic proxy) -> visible to the MMA, all threads past this point.
-__device__ __forceinline__ void publish_operands() {
+// Operand writes (generic proxy) -> visible to the MMA, all threads of the group past here.
+__device__ __forceinline__ void publish_operands(int id) {
     tc::fence_async_smem();
     tc::fence_before();
-    __syncthreads();
+    gsync(id);
     tc::fence_after();
+}
+
+// Bounded wait of a group on an inter-CTA counter (leader polls); uniform result.
+__device__ __forceinline__ bool gwait_geq(const unsigned* ctr, unsigned target, int* status, long long limit, int id,
+                                          int* flag) {
+    if ((threadIdx.x & 255u) == 0) {
+        long long it = 0;
+        int good = 1;
+        while (ld_acquire(ctr) < target) {
+            if (ld_status(status) != 0) { good = 0; break; }
+            if (++it > limit) { atomicOr(status, ST_TIMEOUT); good = 0; break; }
+            __nanosleep(100);
+        }
+        if (good && ld_status(status) != 0) good = 0;
+        *flag = good;
+    }
+    gsync(id);
+    const int r = *flag;
+    gsync(id);
+    return r != 0;
 }
 
 // Scaled FP64 triple [S_q, S_1, T_1] -> true values.  psi was multiplied by 2^f and the
@@ -157,7 +193,7 @@ struct P1Item {
 // Scratch of one X-string: floats [re/im][h = z' >> 13][q][n][m' & 3] with z' & 8191 =
 // (m' << 7) | n and q = m' >> 2 (pass 1 writes 16-byte rows, pass 2 reads 32-byte runs).
 template <int MODE, int RB>
-__global__ void __launch_bounds__(256, 1) sre_tc(TcParams P) {
+__global__ void __launch_bounds__(512, 1) sre_tc(TcParams P) {
     constexpr int M = 7 + RB;         // z' bits above the pass-1 tile
     constexpr int L = 13 + M;
     constexpr int T = 1 << M;         // tiles per X-string (pass 1 and pass 2 alike)
@@ -171,14 +207,17 @@ __global__ void __launch_bounds__(256, 1) sre_tc(TcParams P) {
     extern __shared__ uint8_t smem_raw[];
     __shared__ __align__(8) uint64_t mb_p1, mb_p2, mb_st[4];
     __shared__ uint32_t tmem_slot;
+    __shared__ int gflag[2];
     __shared__ double red64[8][3];
-    const uint32_t tid = threadIdx.x, lane = tid & 31u, warp = tid >> 5;
-    const uint32_t quarter = warp & 3u, half = warp >> 2;
+    const uint32_t tid = threadIdx.x, group = tid >> 8, gtid = tid & 255u;
+    const uint32_t lane = tid & 31u, gwarp = gtid >> 5;
+    const uint32_t quarter = gwarp & 3u, half = gwarp >> 2;
+    const int bid = 1 + (int)group;  // this group's named barrier
     const uint32_t sbase = (tc::smem_u32(smem_raw) + 1023u) & ~1023u;
     const uint32_t sH = sbase + SM_H, sP = sbase + SM_P, sQ = sbase + SM_Q, sST = sbase + SM_ST;
 
     // H_128 image: row n, K-chunk kc holds H[8kc .. 8kc+7][n] = (-1)^popc(k & n) in fp16.
-    for (uint32_t i = tid; i < 128u * 16u; i += 256u) {
+    for (uint32_t i = tid; i < 128u * 16u; i += 512u) {
         const uint32_t n = i >> 4, kc = i & 15u;
         uint32_t w[4];
 #pragma unroll
@@ -190,276 +229,159 @@ __global__ void __launch_bounds__(256, 1) sre_tc(TcParams P) {
         }
         tc::sts128(sH + kmaj(n, kc), make_uint4(w[0], w[1], w[2], w[3]));
     }
-    if (warp == 0) tc::tmem_alloc(&tmem_slot, 256);
+    if (tid < 32) tc::tmem_alloc(&tmem_slot, 256);
     if (tid == 0) {
         tc::mbar_init(&mb_p1, 1);
         tc::mbar_init(&mb_p2, 1);
         for (int b = 0; b < 4; ++b) tc::mbar_init(&mb_st[b], 1);
     }
-    publish_operands();
+    tc::fence_async_smem();
+    tc::fence_before();
+    __syncthreads();
+    tc::fence_after();
     const uint32_t tmem = tmem_slot;
-    const uint32_t t1 = tmem + ((quarter * 32u) << 16);  // D1 / D2, columns [0, 128)
-    const uint32_t t3 = t1 + 128u;                       // D3, columns [128, 256)
-    uint32_t ph1 = 0, ph2 = 0, phs[4] = {0, 0, 0, 0};
-    int pending[4] = {0, 0, 0, 0};  // staged copies issued and not yet consumed, per buffer
+    const uint32_t tq = tmem + ((quarter * 32u) << 16);  // this warp's lane quarter
 
     const float2* __restrict__ psi = P.psi;
     const int64_t dim = int64_t(1) << P.N;
     const int64_t total = (P.n_batches + 2) * T;
-    double accw[3] = {0.0, 0.0, 0.0};  // lane 0 of each warp: FP64 sums of its warp's tiles
+    double accw[3] = {0.0, 0.0, 0.0};  // pass-2 group, lane 0 of each warp: FP64 tile sums
+    bool ok = true;
 
-    // X-string of batch g (-1 if the batch does not exist or the entry is out of range)
+    // X-string of batch g (-1 if the batch does not exist, -2 if the entry is out of range)
     auto xstring = [&](int64_t g) -> int64_t {
         if (g < 0 || g >= P.n_batches || g >= P.count) return -1;
         const int64_t a = P.a_list ? P.a_list[g] : g;
         return (a >= 0 && a < dim) ? a : -2;
     };
-    auto p1_item = [&](int64_t c) {
-        P1Item it;
-        if (c >= total) return it;
-        const int64_t s = c / T;
-        it.h = c % T;
-        const int64_t a = xstring(s);
-        it.a = a;
-        it.far = a >= 8192;
-        return it;
-    };
-    // thread 0: bulk copies of eighth k of a far item (own and partner rows) into buffer k & 3
-    auto stage = [&](const P1Item& it, int k) {
-        const PairRows<13, M> pr(it.a, it.h);
-        const uint32_t buf = sST + (uint32_t)(k & 3) * 16384u;
-        const int64_t jk = (int64_t)k * CHUNK;
-        tc::expect_tx(&mb_st[k & 3], 2u * CHUNK * 8u);
-        tc::bulk_g2s(buf, psi + pr.rowA + jk, CHUNK * 8u, &mb_st[k & 3]);
-        tc::bulk_g2s(buf + 8192u, psi + pr.rowB + (jk ^ (pr.al & 0x1C00)), CHUNK * 8u, &mb_st[k & 3]);
-    };
-    auto stage4 = [&](const P1Item& it) {  // eighths 0..3 (every buffer)
-        if (tid == 0) for (int k = 0; k < 4; ++k) stage(it, k);
-        pending[0] = pending[1] = pending[2] = pending[3] = 1;
-    };
 
-    // pass-2 tile of a work item in registers, loaded one item ahead: the wait for its batch
-    // and the L2 round trip overlap the rest of the previous item
-    float xq[ITER2][1 << RB][8];
-    bool xq_valid = false;
-    auto load_p2 = [&](int64_t c2, float (&xr)[ITER2][1 << RB][8], bool& valid) -> bool {
-        valid = false;
-        if (c2 >= total) return true;
-        const int64_t g = c2 / T - 2;
-        const int r2 = (int)(c2 % T);
-        if (g < 0 || xstring(g) < 0) return true;
-        const int sl = (int)(g % P.R);
-        const unsigned need = (unsigned)((g / P.R + 1) * T) + P.wait_bias;
-        if (!cta_wait_geq(P.done1 + sl, need, P.status, P.spin_limit)) return false;
-        const float* scr = P.scratch + (size_t)sl * ((size_t)2 << L);
-        const uint32_t h7_lo = tid & 7u, rest = tid >> 3;
-#pragma unroll
-        for (int it = 0; it < ITER2; ++it) {
-            const uint32_t combo = rest + 32u * it;
-            const uint32_t oct = combo % OCT, cc = (combo / OCT) & 1u, h7 = ((combo / (2 * OCT)) << 3) | h7_lo;
-#pragma unroll
-            for (int rc = 0; rc < (1 << RB); ++rc)
-                tc::ldcg256(scr + (size_t)cc * ((size_t)1 << L) + (size_t)(h7 + 128u * rc) * 8192u + (size_t)r2 * S + oct * 8u,
-                            xr[it][rc]);
+    if (group == 0) {
+        // ================= pass 1: pair products -> blocks 1 and 2 -> scratch =================
+        uint32_t ph1 = 0, phs[4] = {0, 0, 0, 0};
+        int pending[4] = {0, 0, 0, 0};  // staged copies issued and not yet consumed, per buffer
+        auto p1_item = [&](int64_t c) {
+            P1Item it;
+            if (c >= total) return it;
+            it.h = c % T;
+            it.a = xstring(c / T);
+            it.far = it.a >= 8192;
+            return it;
+        };
+        // leader: bulk copies of eighth k of a far item (own and partner rows) into buffer k & 3
+        auto stage = [&](const P1Item& it, int k) {
+            const PairRows<13, M> pr(it.a, it.h);
+            const uint32_t buf = sST + (uint32_t)(k & 3) * 16384u;
+            const int64_t jk = (int64_t)k * CHUNK;
+            tc::expect_tx(&mb_st[k & 3], 2u * CHUNK * 8u);
+            tc::bulk_g2s(buf, psi + pr.rowA + jk, CHUNK * 8u, &mb_st[k & 3]);
+            tc::bulk_g2s(buf + 8192u, psi + pr.rowB + (jk ^ (pr.al & 0x1C00)), CHUNK * 8u, &mb_st[k & 3]);
+        };
+        auto stage4 = [&](const P1Item& it) {  // eighths 0..3 (every buffer)
+            if (gtid == 0) for (int k = 0; k < 4; ++k) stage(it, k);
+            pending[0] = pending[1] = pending[2] = pending[3] = 1;
+        };
+        P1Item cur = p1_item(blockIdx.x);
+        bool staged = false;  // eighths 0..3 of `cur` are in flight
+        if (cur.far) {
+            stage4(cur);
+            staged = true;
         }
-        valid = true;
-        return true;
-    };
-
-    P1Item cur = p1_item(blockIdx.x);
-    bool staged = false;  // eighths 0..3 of `cur` are in flight
-    if (cur.far) {
-        stage4(cur);
-        staged = true;
-    }
-    bool ok = load_p2(blockIdx.x, xq, xq_valid);
-
-    for (int64_t c = blockIdx.x; c < total && ok; c += gridDim.x) {
-        const int64_t s = c / T;
-        const int r = (int)(c % T);
-        const P1Item nxt = p1_item(c + gridDim.x);
-        const int64_t g1 = s, g2 = s - 2;
-        const bool has1 = g1 < P.n_batches, has2 = g2 >= 0 && g2 < P.n_batches;
-        const int64_t a1 = has1 ? cur.a : -1;
-        if (has1 && a1 == -2 && tid == 0) atomicOr(P.status, ST_BADARG);
-        const bool do1 = a1 >= 0;
-        const int64_t a2 = has2 ? xstring(g2) : -1;
-        const bool do2 = a2 >= 0;
-        const int slot1 = (int)(g1 % P.R), slot2 = has2 ? (int)(g2 % P.R) : 0;
-        float* scr1 = P.scratch + (size_t)slot1 * ((size_t)2 << L);
-        const float* scr2 = P.scratch + (size_t)slot2 * ((size_t)2 << L);
-        bool nxt_staged = false;
-
-        // ---- (a) pass 1: pair products -> block-1 operand (MN-major, swizzled) -> MMA1 ------
-        if (do1) {
-            const uint32_t a_hi = sP, a_lo = sP + 32768u;
-            if (cur.far) {
-                if (!staged) stage4(cur);
-                const uint32_t al_lo = (uint32_t)(PairRows<13, M>(cur.a, cur.h).al) & (CHUNK - 1u);
-                // eighth k holds m6 in [8k, 8k + 8) (fibre group k); step p: thread (n, hh)
-                // builds fibre group 2p + hh from eighth 2p + hh
-                const uint32_t n = tid & 127u, hh = tid >> 7;
-                for (int p = 0; p < 4 && ok; ++p) {
-                    const int b0 = (2 * p) & 3, b1 = (2 * p + 1) & 3;
-                    ok = wait_bar(&mb_st[b0], phs[b0], P.status, P.spin_limit) &&
-                         wait_bar(&mb_st[b1], phs[b1], P.status, P.spin_limit);
-                    pending[b0] = pending[b1] = 0;
-                    if (!ok) break;
-                    const uint32_t own = sST + (uint32_t)((2 * p + hh) & 3) * 16384u, par = own + 8192u;
-                    float re[8], im[8];
+        for (int64_t c = blockIdx.x; c < total && ok; c += gridDim.x) {
+            const int64_t g1 = c / T;
+            const P1Item nxt = p1_item(c + gridDim.x);
+            bool nxt_staged = false;
+            if (g1 >= P.n_batches) { cur = nxt; staged = false; continue; }  // group-uniform
+            const int64_t a1 = cur.a;
+            if (a1 == -2 && gtid == 0) atomicOr(P.status, ST_BADARG);
+            const bool do1 = a1 >= 0;
+            const int slot1 = (int)(g1 % P.R);
+            float* scr1 = P.scratch + (size_t)slot1 * ((size_t)2 << L);
+            if (do1) {
+                // ---- block 1 operand (MN-major, swizzled) from staged or directly loaded rows ----
+                const uint32_t a_hi = sP, a_lo = sP + 32768u;
+                if (cur.far) {
+                    if (!staged) stage4(cur);
+                    const uint32_t al_lo = (uint32_t)(PairRows<13, M>(cur.a, cur.h).al) & (CHUNK - 1u);
+                    // eighth k holds m6 in [8k, 8k + 8) (fibre group k); step p: thread (n, hh)
+                    // builds fibre group 2p + hh from eighth 2p + hh
+                    const uint32_t n = gtid & 127u, hh = gtid >> 7;
+                    for (int p = 0; p < 4 && ok; ++p) {
+                        const int b0 = (2 * p) & 3, b1 = (2 * p + 1) & 3;
+                        ok = wait_bar(&mb_st[b0], phs[b0], P.status, P.spin_limit, bid) &&
+                             wait_bar(&mb_st[b1], phs[b1], P.status, P.spin_limit, bid);
+                        pending[b0] = pending[b1] = 0;
+                        if (!ok) break;
+                        const uint32_t own = sST + (uint32_t)((2 * p + hh) & 3) * 16384u, par = own + 8192u;
+                        float re[8], im[8];
 #pragma unroll
-                    for (int e = 0; e < 8; ++e) {
-                        const uint32_t jl = ((uint32_t)e << 7) | n;  // j & 1023
-                        const float2 u = tc::lds64(own + jl * 8u);
-                        const float2 v = tc::lds64(par + (jl ^ al_lo) * 8u);
-                        const float2 w = conj_mul(v, u);
-                        re[e] = w.x;
-                        im[e] = w.y;
-                    }
-                    put_block1(re, im, 2u * p + hh, n, a_hi, a_lo);
-                    __syncthreads();  // buffers b0, b1 consumed
-                    if (p < 2 || nxt.far) {
-                        if (tid == 0) {
-                            if (p < 2) { stage(cur, 2 * p + 4); stage(cur, 2 * p + 5); }
-                            else { stage(nxt, 2 * p - 4); stage(nxt, 2 * p - 3); }
+                        for (int e = 0; e < 8; ++e) {
+                            const uint32_t jl = ((uint32_t)e << 7) | n;  // j & 1023
+                            const float2 u = tc::lds64(own + jl * 8u);
+                            const float2 v = tc::lds64(par + (jl ^ al_lo) * 8u);
+                            const float2 w = conj_mul(v, u);
+                            re[e] = w.x;
+                            im[e] = w.y;
                         }
-                        pending[b0] = pending[b1] = 1;
-                    }
-                }
-                nxt_staged = nxt.far;
-            } else {
-                produce_near<M>(psi, PairRows<13, M>(cur.a, cur.h), cur.a, tid, a_hi, a_lo);
-            }
-            if (!ok) break;
-            publish_operands();
-            if (tid == 0) {
-                issue_block<8, SW_LBO, SW_SBO, SW_STEP, 2>(tmem, a_hi, a_lo, sH, ID_B1);
-                tc::commit(&mb_p1);
-            }
-        }
-        if (!nxt_staged && nxt.far) {  // this item staged nothing for the next one
-            stage4(nxt);
-            nxt_staged = true;
-        }
-
-        // ---- (b) pass 2: scratch -> butterflies over bits [20, L) -> block-3 operand -> MMA3 ----
-        if (do2) {
-            // xq holds this tile (loaded at the end of the previous item, after its batch's wait)
-            const uint32_t q_hi = sQ, q_lo = sQ + 32768u;
-            const uint32_t h7_lo = tid & 7u, rest = tid >> 3;
-#pragma unroll
-            for (int it = 0; it < ITER2; ++it) {
-                const uint32_t combo = rest + 32u * it;
-                const uint32_t oct = combo % OCT, cc = (combo / OCT) & 1u, h7 = ((combo / (2 * OCT)) << 3) | h7_lo;
-                float (&x)[1 << RB][8] = xq[it];
-#pragma unroll
-                for (int b = 0; b < RB; ++b)
-#pragma unroll
-                    for (int rc = 0; rc < (1 << RB); ++rc)
-                        if (!(rc & (1 << b))) {
-#pragma unroll
-                            for (int e = 0; e < 8; e += 2) {
-                                const float2 p = make_float2(x[rc][e], x[rc][e + 1]);
-                                const float2 q = make_float2(x[rc | (1 << b)][e], x[rc | (1 << b)][e + 1]);
-                                const float2 s0 = add2(p, q), s1 = sub2(p, q);
-                                x[rc][e] = s0.x; x[rc][e + 1] = s0.y;
-                                x[rc | (1 << b)][e] = s1.x; x[rc | (1 << b)][e + 1] = s1.y;
+                        put_block1(re, im, 2u * p + hh, n, a_hi, a_lo);
+                        gsync(bid);  // buffers b0, b1 consumed
+                        if (p < 2 || nxt.far) {
+                            if (gtid == 0) {
+                                if (p < 2) { stage(cur, 2 * p + 4); stage(cur, 2 * p + 5); }
+                                else { stage(nxt, 2 * p - 4); stage(nxt, 2 * p - 3); }
                             }
+                            pending[b0] = pending[b1] = 1;
                         }
-#pragma unroll
-                for (int rc = 0; rc < (1 << RB); ++rc) {
-                    uint4 hi, lo;
-                    tc::split8(x[rc], hi, lo);
-                    const uint32_t o = mnmaj(((rc * 2u + cc) * S + oct * 8u) >> 3, h7);
-                    tc::sts128(q_hi + o, hi);
-                    tc::sts128(q_lo + o, lo);
+                    }
+                    nxt_staged = nxt.far;
+                } else {
+                    produce_near<M>(psi, PairRows<13, M>(cur.a, cur.h), cur.a, gtid, a_hi, a_lo);
+                }
+                if (!ok) break;
+                publish_operands(bid);
+                if (gtid == 0) {
+                    issue_block<8, SW_LBO, SW_SBO, SW_STEP, 2>(tmem, a_hi, a_lo, sH, ID_B1);
+                    tc::commit(&mb_p1);
                 }
             }
-            publish_operands();
-            if (tid == 0) {
-                issue_block<8, MN_LBO, MN_SBO, MN_STEP, 0>(tmem + 128u, q_hi, q_lo, sH, ID_B3);
-                tc::commit(&mb_p2);
-                // the tile's scratch has been read: the slot may be refilled
-                red_release_add(P.done2 + slot2, 1u);
-            }
-            if constexpr (S * 4 >= 128) {
-                // drop the tile's lines from L2 unwritten
-                constexpr int LPR = (S * 4) / 128;
-                for (int qd = tid; qd < 2 * (1 << M) * LPR; qd += 256) {
-                    const int row = qd / LPR;  // (re/im, h)
-                    discard_l2_line(scr2 + (size_t)row * 8192u + (size_t)r * S + (qd % LPR) * 32);
-                }
-            }
-        } else if (has2 && tid == 0) {
-            red_release_add(P.done2 + slot2, 1u);  // nothing to read (invalid entry): keep counts
-        }
-
-        // ---- (c) pass 1: block-1 result -> block-2 operand (MN-major) -> MMA2 -----------------
-        if (do1) {
-            if (!wait_bar(&mb_p1, ph1, P.status, P.spin_limit)) { ok = false; break; }
-            const uint32_t row = quarter * 32u + lane, cc = row >> 6, m6 = row & 63u;
-            float v[64];
-            tc::tmem_ld32(t1 + half * 64u, *reinterpret_cast<float(*)[32]>(v));
-            tc::tmem_ld32(t1 + half * 64u + 32u, *reinterpret_cast<float(*)[32]>(v + 32));
-            tc::tmem_wait_ld();
-            const uint32_t b_hi = sP + cc * 32768u, b_lo = b_hi + 16384u;
-#pragma unroll
-            for (int gq = 0; gq < 8; ++gq) {
-                uint4 hi, lo;
-                tc::split8(v + 8 * gq, hi, lo);
-                const uint32_t o = mnmaj(half * 8u + gq, m6);
-                tc::sts128(b_hi + o, hi);
-                tc::sts128(b_lo + o, lo);
-            }
-            publish_operands();
-            if (tid == 0) {
-                issue_block<4, MN_LBO, MN_SBO, MN_STEP, 0>(tmem, sP, sP + 16384u, sH, ID_B2);
-                issue_block<4, MN_LBO, MN_SBO, MN_STEP, 0>(tmem + 64u, sP + 32768u, sP + 49152u, sH, ID_B2);
-                tc::commit(&mb_p1);
-            }
-        }
-
-        // ---- (d) pass 2: block-3 result -> sum of |.|^{2n} ---------------------------------
-        if (do2) {
-            if (!wait_bar(&mb_p2, ph2, P.status, P.spin_limit)) { ok = false; break; }
-            float v[64];
-            tc::tmem_ld32(t3 + half * 64u, *reinterpret_cast<float(*)[32]>(v));
-            tc::tmem_ld32(t3 + half * 64u + 32u, *reinterpret_cast<float(*)[32]>(v + 32));
-            tc::tmem_wait_ld();
-            tc::fence_before();
-            Acc<MODE> ac;
-#pragma unroll
-            for (int k = 0; k < 32; ++k) {
-                float2 w = make_float2(v[2 * k], v[2 * k + 1]);
-                if constexpr (RS != 0) w = mul2(w, make_float2(RSF, RSF));
-                ac.add(w, P.nq);
-            }
-            ac.fold();
-            float q = ac.q, s1 = ac.s1, uu = ac.u;
-            double qd = ac.qd;
-            warp_sum3<MODE>(q, s1, uu, qd, 32);
-            if (lane == 0) {
-                // FP32 warp partial -> FP64; warps accumulate independently (no block barrier)
-                double vv[3];
-                finish3<MODE>(q, s1, uu, qd, P.nq, vv);
-                if (P.per_a) unscale<MODE, RS>(vv, *P.scale_exp, P.nq, P.out + (((size_t)g2 * T + r) * 8 + warp) * 3);
-                else { accw[0] += vv[0]; accw[1] += vv[1]; accw[2] += vv[2]; }
-            }
-        }
-
-        // ---- (e) pass 1: block-2 result (rows n, cols (re/im, m')) -> scratch ---------------
-        if (has1) {
-            // the slot is free once pass 2 of batch g1 - R has read it
-            if (g1 >= P.R) {
-                const unsigned need = (unsigned)((g1 / P.R) * T) + P.wait_bias;
-                if (!cta_wait_geq(P.done2 + slot1, need, P.status, P.spin_limit)) { ok = false; break; }
+            if (!nxt_staged && nxt.far) {  // this item staged nothing for the next one
+                stage4(nxt);
+                nxt_staged = true;
             }
             if (do1) {
-                if (!wait_bar(&mb_p1, ph1, P.status, P.spin_limit)) { ok = false; break; }
+                // ---- block 1 result (rows (re/im, m6), cols n) -> block 2 operand -> MMA2 ----
+                if (!wait_bar(&mb_p1, ph1, P.status, P.spin_limit, bid)) { ok = false; break; }
+                const uint32_t row = quarter * 32u + lane, cc = row >> 6, m6 = row & 63u;
+                float v[64];
+                tc::tmem_ld32(tq + half * 64u, *reinterpret_cast<float(*)[32]>(v));
+                tc::tmem_ld32(tq + half * 64u + 32u, *reinterpret_cast<float(*)[32]>(v + 32));
+                tc::tmem_wait_ld();
+                const uint32_t b_hi = sP + cc * 32768u, b_lo = b_hi + 16384u;
+#pragma unroll
+                for (int gq = 0; gq < 8; ++gq) {
+                    uint4 hi, lo;
+                    tc::split8(v + 8 * gq, hi, lo);
+                    const uint32_t o = mnmaj(half * 8u + gq, m6);
+                    tc::sts128(b_hi + o, hi);
+                    tc::sts128(b_lo + o, lo);
+                }
+                publish_operands(bid);
+                if (gtid == 0) {
+                    issue_block<4, MN_LBO, MN_SBO, MN_STEP, 0>(tmem, sP, sP + 16384u, sH, ID_B2);
+                    issue_block<4, MN_LBO, MN_SBO, MN_STEP, 0>(tmem + 64u, sP + 32768u, sP + 49152u, sH, ID_B2);
+                    tc::commit(&mb_p1);
+                }
+            }
+            // ---- block 2 result (rows n, cols (re/im, m')) -> scratch, then release ----------
+            if (g1 >= P.R) {  // the slot is free once pass 2 of batch g1 - R has read it
+                const unsigned need = (unsigned)((g1 / P.R) * T) + P.wait_bias;
+                if (!gwait_geq(P.done2 + slot1, need, P.status, P.spin_limit, bid, &gflag[0])) { ok = false; break; }
+            }
+            if (do1) {
+                if (!wait_bar(&mb_p1, ph1, P.status, P.spin_limit, bid)) { ok = false; break; }
                 const uint32_t n = quarter * 32u + lane, cc = half;
                 float v[64];
-                tc::tmem_ld32(t1 + cc * 64u, *reinterpret_cast<float(*)[32]>(v));
-                tc::tmem_ld32(t1 + cc * 64u + 32u, *reinterpret_cast<float(*)[32]>(v + 32));
+                tc::tmem_ld32(tq + cc * 64u, *reinterpret_cast<float(*)[32]>(v));
+                tc::tmem_ld32(tq + cc * 64u + 32u, *reinterpret_cast<float(*)[32]>(v + 32));
                 tc::tmem_wait_ld();
                 tc::fence_before();
                 float* dst = scr1 + (size_t)cc * ((size_t)1 << L) + (size_t)cur.h * 8192u + n * 4u;
@@ -468,23 +390,115 @@ __global__ void __launch_bounds__(256, 1) sre_tc(TcParams P) {
                     __stcg(reinterpret_cast<float4*>(dst + q * 512),
                            make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
             }
-            __syncthreads();
-            if (tid == 0) red_release_add(P.done1 + slot1, 1u);
+            gsync(bid);
+            if (gtid == 0) red_release_add(P.done1 + slot1, 1u);
+            cur = nxt;
+            staged = nxt_staged;
         }
-        // ---- (f) next item's pass-2 tile: wait for its batch, load it into registers --------
-        if (ok) ok = load_p2(c + gridDim.x, xq, xq_valid);
-        cur = nxt;
-        staged = nxt_staged;
+        // drain staged copies (error exits)
+        for (int b = 0; b < 4; ++b)
+            if (pending[b]) tc::mbar_wait(&mb_st[b], phs[b], P.spin_limit);
+    } else {
+        // ================= pass 2: scratch -> block 3 -> sum of |.|^{2n} ======================
+        uint32_t ph2 = 0;
+        for (int64_t c = blockIdx.x; c < total && ok; c += gridDim.x) {
+            const int64_t g2 = c / T - 2;
+            const int r = (int)(c % T);
+            if (g2 < 0 || g2 >= P.n_batches) continue;  // group-uniform
+            const int slot2 = (int)(g2 % P.R);
+            const bool do2 = xstring(g2) >= 0;
+            if (do2) {
+                const unsigned need = (unsigned)((g2 / P.R + 1) * T) + P.wait_bias;
+                if (!gwait_geq(P.done1 + slot2, need, P.status, P.spin_limit, bid, &gflag[1])) { ok = false; break; }
+                const float* scr2 = P.scratch + (size_t)slot2 * ((size_t)2 << L);
+                const uint32_t q_hi = sQ, q_lo = sQ + 32768u;
+                const uint32_t h7_lo = gtid & 7u, rest = gtid >> 3;
+#pragma unroll
+                for (int it = 0; it < ITER2; ++it) {
+                    const uint32_t combo = rest + 32u * it;
+                    const uint32_t oct = combo % OCT, cc = (combo / OCT) & 1u, h7 = ((combo / (2 * OCT)) << 3) | h7_lo;
+                    float x[1 << RB][8];
+#pragma unroll
+                    for (int rc = 0; rc < (1 << RB); ++rc)
+                        tc::ldcg256(scr2 + (size_t)cc * ((size_t)1 << L) + (size_t)(h7 + 128u * rc) * 8192u +
+                                        (size_t)r * S + oct * 8u,
+                                    x[rc]);
+#pragma unroll
+                    for (int b = 0; b < RB; ++b)
+#pragma unroll
+                        for (int rc = 0; rc < (1 << RB); ++rc)
+                            if (!(rc & (1 << b))) {
+#pragma unroll
+                                for (int e = 0; e < 8; e += 2) {
+                                    const float2 p = make_float2(x[rc][e], x[rc][e + 1]);
+                                    const float2 q = make_float2(x[rc | (1 << b)][e], x[rc | (1 << b)][e + 1]);
+                                    const float2 s0 = add2(p, q), s1 = sub2(p, q);
+                                    x[rc][e] = s0.x; x[rc][e + 1] = s0.y;
+                                    x[rc | (1 << b)][e] = s1.x; x[rc | (1 << b)][e + 1] = s1.y;
+                                }
+                            }
+#pragma unroll
+                    for (int rc = 0; rc < (1 << RB); ++rc) {
+                        uint4 hi, lo;
+                        tc::split8(x[rc], hi, lo);
+                        const uint32_t o = mnmaj(((rc * 2u + cc) * S + oct * 8u) >> 3, h7);
+                        tc::sts128(q_hi + o, hi);
+                        tc::sts128(q_lo + o, lo);
+                    }
+                }
+                publish_operands(bid);
+                if (gtid == 0) {
+                    issue_block<8, MN_LBO, MN_SBO, MN_STEP, 0>(tmem + 128u, q_hi, q_lo, sH, ID_B3);
+                    tc::commit(&mb_p2);
+                }
+                if constexpr (S * 4 >= 128) {
+                    // drop the tile's lines from L2 unwritten
+                    constexpr int LPR = (S * 4) / 128;
+                    for (int qd = gtid; qd < 2 * (1 << M) * LPR; qd += 256) {
+                        const int row = qd / LPR;  // (re/im, h)
+                        discard_l2_line(scr2 + (size_t)row * 8192u + (size_t)r * S + (qd % LPR) * 32);
+                    }
+                }
+                // the tile's scratch has been read and dropped: the slot may be refilled (the
+                // release must follow the discards, or a refill could land before a discard)
+                gsync(bid);
+                if (gtid == 0) red_release_add(P.done2 + slot2, 1u);
+                if (!wait_bar(&mb_p2, ph2, P.status, P.spin_limit, bid)) { ok = false; break; }
+                float v[64];
+                tc::tmem_ld32(tq + 128u + half * 64u, *reinterpret_cast<float(*)[32]>(v));
+                tc::tmem_ld32(tq + 128u + half * 64u + 32u, *reinterpret_cast<float(*)[32]>(v + 32));
+                tc::tmem_wait_ld();
+                tc::fence_before();
+                Acc<MODE> ac;
+#pragma unroll
+                for (int k = 0; k < 32; ++k) {
+                    float2 w = make_float2(v[2 * k], v[2 * k + 1]);
+                    if constexpr (RS != 0) w = mul2(w, make_float2(RSF, RSF));
+                    ac.add(w, P.nq);
+                }
+                ac.fold();
+                float q = ac.q, s1 = ac.s1, uu = ac.u;
+                double qd = ac.qd;
+                warp_sum3<MODE>(q, s1, uu, qd, 32);
+                if (lane == 0) {
+                    // FP32 warp partial -> FP64; warps accumulate independently
+                    double vv[3];
+                    finish3<MODE>(q, s1, uu, qd, P.nq, vv);
+                    if (P.per_a) unscale<MODE, RS>(vv, *P.scale_exp, P.nq, P.out + (((size_t)g2 * T + r) * 8 + gwarp) * 3);
+                    else { accw[0] += vv[0]; accw[1] += vv[1]; accw[2] += vv[2]; }
+                }
+            } else if (gtid == 0) {
+                red_release_add(P.done2 + slot2, 1u);  // nothing to read (invalid entry): keep counts
+            }
+        }
     }
-    // every exit path: no MMA is in flight (each commit was waited on); drain staged copies
-    for (int b = 0; b < 4; ++b)
-        if (pending[b]) tc::mbar_wait(&mb_st[b], phs[b], P.spin_limit);
+    // both groups done: no MMA is in flight (each commit was waited on)
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (warp == 0) tc::tmem_dealloc(tmem, 256);
+    if (tid < 32) tc::tmem_dealloc(tmem, 256);
     if (!P.per_a) {
-        if (lane == 0) { red64[warp][0] = accw[0]; red64[warp][1] = accw[1]; red64[warp][2] = accw[2]; }
+        if (group == 1 && lane == 0) { red64[gwarp][0] = accw[0]; red64[gwarp][1] = accw[1]; red64[gwarp][2] = accw[2]; }
         __syncthreads();
         if (tid == 0) {
             double acc[3] = {0.0, 0.0, 0.0};
@@ -533,7 +547,7 @@ static cudaError_t tc_prep(int* occ) {
     // two CTAs of ~97 KiB per SM need the largest shared-memory carveout
     e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, 256, SM_DYN);
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, 512, SM_DYN);
 }
 
 template <int MODE>
@@ -542,7 +556,7 @@ static cudaError_t tc_dispatch(const TcParams* P, int N, int* occ, int grid, cud
 #define HM_CASE(NN)                                                                 \
     case NN:                                                                        \
         if (occ) return tc_prep<MODE, NN - 21>(occ);                                \
-        sre_tc<MODE, NN - 21><<<grid, 256, SM_DYN, st>>>(*P);                        \
+        sre_tc<MODE, NN - 21><<<grid, 512, SM_DYN, st>>>(*P);                        \
         return cudaGetLastError();
         HM_CASE(21) HM_CASE(22) HM_CASE(23) HM_CASE(24)
 #undef HM_CASE
