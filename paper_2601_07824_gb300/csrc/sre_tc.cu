@@ -205,7 +205,7 @@ __global__ void __launch_bounds__(512, 1) sre_tc(TcParams P) {
     constexpr int RS = MODE == 3 ? 8 : 0;
     constexpr float RSF = MODE == 3 ? 1.f / 256.f : 1.f;
     extern __shared__ uint8_t smem_raw[];
-    __shared__ __align__(8) uint64_t mb_p1, mb_p2, mb_st[4];
+    __shared__ __align__(8) uint64_t mb_p1, mb_p2, mb_d2full, mb_d2free, mb_st[4];
     __shared__ uint32_t tmem_slot;
     __shared__ int gflag[2];
     __shared__ double red64[8][3];
@@ -229,10 +229,12 @@ __global__ void __launch_bounds__(512, 1) sre_tc(TcParams P) {
         }
         tc::sts128(sH + kmaj(n, kc), make_uint4(w[0], w[1], w[2], w[3]));
     }
-    if (tid < 32) tc::tmem_alloc(&tmem_slot, 256);
+    if (tid < 32) tc::tmem_alloc(&tmem_slot, 512);
     if (tid == 0) {
         tc::mbar_init(&mb_p1, 1);
         tc::mbar_init(&mb_p2, 1);
+        tc::mbar_init(&mb_d2full, 1);
+        tc::mbar_init(&mb_d2free, 1);
         for (int b = 0; b < 4; ++b) tc::mbar_init(&mb_st[b], 1);
     }
     tc::fence_async_smem();
@@ -256,8 +258,11 @@ __global__ void __launch_bounds__(512, 1) sre_tc(TcParams P) {
     };
 
     if (group == 0) {
-        // ================= pass 1: pair products -> blocks 1 and 2 -> scratch =================
-        uint32_t ph1 = 0, phs[4] = {0, 0, 0, 0};
+        // ================= pass 1: pair products -> blocks 1 and 2 (the store of block 2 is
+        // done by the pass-2 group, which frees its accumulator through mb_d2free) ============
+        uint32_t ph1 = 0, phs[4] = {0, 0, 0, 0}, ph_full = 0, ph_free = 0;
+        bool mma2_out = false;  // an MMA2 was issued whose completion this group has not seen
+        bool d2_used = false;   // block-2 accumulator holds a tile the pass-2 group must store
         int pending[4] = {0, 0, 0, 0};  // staged copies issued and not yet consumed, per buffer
         auto p1_item = [&](int64_t c) {
             P1Item it;
@@ -294,9 +299,12 @@ __global__ void __launch_bounds__(512, 1) sre_tc(TcParams P) {
             const int64_t a1 = cur.a;
             if (a1 == -2 && gtid == 0) atomicOr(P.status, ST_BADARG);
             const bool do1 = a1 >= 0;
-            const int slot1 = (int)(g1 % P.R);
-            float* scr1 = P.scratch + (size_t)slot1 * ((size_t)2 << L);
             if (do1) {
+                // the previous MMA2 read its operand from the region block 1 is about to overwrite
+                if (mma2_out) {
+                    if (!wait_bar(&mb_d2full, ph_full, P.status, P.spin_limit, bid)) { ok = false; break; }
+                    mma2_out = false;
+                }
                 // ---- block 1 operand (MN-major, swizzled) from staged or directly loaded rows ----
                 const uint32_t a_hi = sP, a_lo = sP + 32768u;
                 if (cur.far) {
@@ -364,49 +372,33 @@ __global__ void __launch_bounds__(512, 1) sre_tc(TcParams P) {
                     tc::sts128(b_hi + o, hi);
                     tc::sts128(b_lo + o, lo);
                 }
+                // the block-2 accumulator must have been read out by the pass-2 group
+                if (d2_used && !wait_bar(&mb_d2free, ph_free, P.status, P.spin_limit, bid)) { ok = false; break; }
                 publish_operands(bid);
                 if (gtid == 0) {
-                    issue_block<4, MN_LBO, MN_SBO, MN_STEP, 0>(tmem, sP, sP + 16384u, sH, ID_B2);
-                    issue_block<4, MN_LBO, MN_SBO, MN_STEP, 0>(tmem + 64u, sP + 32768u, sP + 49152u, sH, ID_B2);
-                    tc::commit(&mb_p1);
+                    issue_block<4, MN_LBO, MN_SBO, MN_STEP, 0>(tmem + 256u, sP, sP + 16384u, sH, ID_B2);
+                    issue_block<4, MN_LBO, MN_SBO, MN_STEP, 0>(tmem + 320u, sP + 32768u, sP + 49152u, sH, ID_B2);
+                    tc::commit(&mb_d2full);
                 }
+                mma2_out = true;
+                d2_used = true;
             }
-            // ---- block 2 result (rows n, cols (re/im, m')) -> scratch, then release ----------
-            if (g1 >= P.R) {  // the slot is free once pass 2 of batch g1 - R has read it
-                const unsigned need = (unsigned)((g1 / P.R) * T) + P.wait_bias;
-                if (!gwait_geq(P.done2 + slot1, need, P.status, P.spin_limit, bid, &gflag[0])) { ok = false; break; }
-            }
-            if (do1) {
-                if (!wait_bar(&mb_p1, ph1, P.status, P.spin_limit, bid)) { ok = false; break; }
-                const uint32_t n = quarter * 32u + lane, cc = half;
-                float v[64];
-                tc::tmem_ld32(tq + cc * 64u, *reinterpret_cast<float(*)[32]>(v));
-                tc::tmem_ld32(tq + cc * 64u + 32u, *reinterpret_cast<float(*)[32]>(v + 32));
-                tc::tmem_wait_ld();
-                tc::fence_before();
-                float* dst = scr1 + (size_t)cc * ((size_t)1 << L) + (size_t)cur.h * 8192u + n * 4u;
-#pragma unroll
-                for (int q = 0; q < 16; ++q)
-                    __stcg(reinterpret_cast<float4*>(dst + q * 512),
-                           make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
-            }
-            gsync(bid);
-            if (gtid == 0) red_release_add(P.done1 + slot1, 1u);
             cur = nxt;
             staged = nxt_staged;
         }
-        // drain staged copies (error exits)
+        // drain staged copies (error exits) and the last MMA2
         for (int b = 0; b < 4; ++b)
             if (pending[b]) tc::mbar_wait(&mb_st[b], phs[b], P.spin_limit);
+        if (mma2_out) tc::mbar_wait(&mb_d2full, ph_full, P.spin_limit);
     } else {
         // ================= pass 2: scratch -> block 3 -> sum of |.|^{2n} ======================
-        uint32_t ph2 = 0;
+        uint32_t ph2 = 0, ph_full = 0;
         for (int64_t c = blockIdx.x; c < total && ok; c += gridDim.x) {
             const int64_t g2 = c / T - 2;
             const int r = (int)(c % T);
-            if (g2 < 0 || g2 >= P.n_batches) continue;  // group-uniform
-            const int slot2 = (int)(g2 % P.R);
-            const bool do2 = xstring(g2) >= 0;
+            const bool has2 = g2 >= 0 && g2 < P.n_batches;  // group-uniform
+            const int slot2 = has2 ? (int)(g2 % P.R) : 0;
+            const bool do2 = has2 && xstring(g2) >= 0;
             if (do2) {
                 const unsigned need = (unsigned)((g2 / P.R + 1) * T) + P.wait_bias;
                 if (!gwait_geq(P.done1 + slot2, need, P.status, P.spin_limit, bid, &gflag[1])) { ok = false; break; }
@@ -487,8 +479,36 @@ __global__ void __launch_bounds__(512, 1) sre_tc(TcParams P) {
                     if (P.per_a) unscale<MODE, RS>(vv, *P.scale_exp, P.nq, P.out + (((size_t)g2 * T + r) * 8 + gwarp) * 3);
                     else { accw[0] += vv[0]; accw[1] += vv[1]; accw[2] += vv[2]; }
                 }
-            } else if (gtid == 0) {
+            } else if (has2 && gtid == 0) {
                 red_release_add(P.done2 + slot2, 1u);  // nothing to read (invalid entry): keep counts
+            }
+            // ---- pass-1 tile of this item: block-2 result (rows n, cols (re/im, m')) -> scratch ----
+            const int64_t g1 = c / T;
+            if (g1 < P.n_batches) {
+                const int slot1 = (int)(g1 % P.R);
+                if (g1 >= P.R) {  // the slot is free once pass 2 of batch g1 - R has read it
+                    const unsigned need = (unsigned)((g1 / P.R) * T) + P.wait_bias;
+                    if (!gwait_geq(P.done2 + slot1, need, P.status, P.spin_limit, bid, &gflag[1])) { ok = false; break; }
+                }
+                if (xstring(g1) >= 0) {
+                    if (!wait_bar(&mb_d2full, ph_full, P.status, P.spin_limit, bid)) { ok = false; break; }
+                    float* scr1 = P.scratch + (size_t)slot1 * ((size_t)2 << L);
+                    const uint32_t n = quarter * 32u + lane, cc = half;
+                    float v[64];
+                    tc::tmem_ld32(tq + 256u + cc * 64u, *reinterpret_cast<float(*)[32]>(v));
+                    tc::tmem_ld32(tq + 256u + cc * 64u + 32u, *reinterpret_cast<float(*)[32]>(v + 32));
+                    tc::tmem_wait_ld();
+                    tc::fence_before();
+                    gsync(bid);
+                    if (gtid == 0) tc::mbar_arrive(&mb_d2free);  // the accumulator may be rewritten
+                    float* dst = scr1 + (size_t)cc * ((size_t)1 << L) + (size_t)(c % T) * 8192u + n * 4u;
+#pragma unroll
+                    for (int q = 0; q < 16; ++q)
+                        __stcg(reinterpret_cast<float4*>(dst + q * 512),
+                               make_float4(v[4 * q], v[4 * q + 1], v[4 * q + 2], v[4 * q + 3]));
+                }
+                gsync(bid);
+                if (gtid == 0) red_release_add(P.done1 + slot1, 1u);
             }
         }
     }
@@ -496,7 +516,7 @@ __global__ void __launch_bounds__(512, 1) sre_tc(TcParams P) {
     tc::fence_before();
     __syncthreads();
     tc::fence_after();
-    if (tid < 32) tc::tmem_dealloc(tmem, 256);
+    if (tid < 32) tc::tmem_dealloc(tmem, 512);
     if (!P.per_a) {
         if (group == 1 && lane == 0) { red64[gwarp][0] = accw[0]; red64[gwarp][1] = accw[1]; red64[gwarp][2] = accw[2]; }
         __syncthreads();
