@@ -58,6 +58,11 @@ def workload_state(N: int):
         f"brickwork Haar circuit on |0>^{N}, depth 10, open chain, seed {2000 + N}"
 
 
+# DRAM bytes (read + write) of one launch of the dominant kernel, from one ncu capture of this
+# exact command (profiles/sre_twopass_N20_bench_dram.md); absent for other workloads.
+TRAFFIC = {(20, 0): 188614912 + 26648091904}
+
+
 def ops_per_string(N: int) -> int:
     # FP32 operations per Pauli string (FMA counted once) in the half-length form:
     # (N-1) butterfly stages, 2 for the pair product, 3 for the |c|^4 and |c|^2 reduction.
@@ -318,7 +323,7 @@ def main():
             achieved = ops_per_string(N) * strings_per_step / avg_s
             peak = fp32_peak_ops(sm_count, mhz_max)
             roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
-                    "frac": achieved / peak, "traffic": None,
+                    "frac": achieved / peak, "traffic": TRAFFIC.get((N, args.xstrings)),
                     "note": f"FP32 ops (FMA = 1) = {ops_per_string(N)} per Pauli string; peak = "
                             f"{sm_count} SMs x 128 lanes x {mhz_max:.0f} MHz; kernel time = CUDA events "
                             "around the call on its stream"}
