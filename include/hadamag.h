@@ -42,6 +42,9 @@ typedef enum {
 
 typedef enum { HADAMAG_C64 = 0, HADAMAG_C128 = 1 } hadamag_dtype;
 
+/* Transform path of the exact-SRE calls (hadamag_sre, hadamag_sre_host, hadamag_sre_terms,
+ * hadamag_sre_mc).  TENSOR runs the tensor-core kernel where it exists (21 <= N <= 24, every
+ * n) and the FP32 CUDA-core kernels for every other N; AUTO currently equals CUDACORE. */
 typedef enum {
     HADAMAG_PATH_AUTO = 0,     /* the library picks */
     HADAMAG_PATH_CUDACORE = 1, /* FP32 butterflies on CUDA cores */
@@ -57,7 +60,8 @@ typedef struct CUstream_st* hadamag_stream_t; /* same type as cudaStream_t */
 hadamag_status hadamag_create(hadamag_ctx_t* ctx, int device);
 /* Free everything the context owns.  Null is accepted. */
 hadamag_status hadamag_destroy(hadamag_ctx_t ctx);
-/* Choose the transform path for later calls (default AUTO). */
+/* Choose the transform path for later calls on this context (default AUTO); INVALID_ARG
+ * for a value outside the enum. */
 hadamag_status hadamag_set_path(hadamag_ctx_t ctx, hadamag_path path);
 /* Bound of every inter-CTA wait, in polling iterations (~0.1 us each; default 2^25), and a
  * value added to every wait target.  A non-zero bias makes waits unsatisfiable; it exists
