@@ -151,6 +151,22 @@ class ClockSampler:
                 "samples": len(mhz)}
 
 
+def max_over_ranks(t_local: float, world: int, device=None) -> float:
+    """The slowest rank's time (all-reduce MAX over the default process group when world > 1)."""
+    if world <= 1:
+        return float(t_local)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(t_local)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def aggregate_rate(world: int, steps: int, units_per_step: float, t_max: float) -> float:
+    """Whole-job throughput: every rank processes `units_per_step` per step (weak scaling)."""
+    return world * steps * units_per_step / t_max
+
+
 def _calibrate(oracle, psi_np, dim, threads, rng):
     """Seconds per X-string of the oracle on this host (probe grown until it takes >= 0.3 s)."""
     count = max(threads, 4)
@@ -196,7 +212,8 @@ def run_reference(args):
     dim = 2 ** N
     rng = np.random.default_rng(777)
     per_a = _calibrate(oracle, psi, dim, threads, rng)
-    budget = max(2.0, 120.0 / max(1, args.steps + args.warmup))
+    # whole run ~ 8 x --cpu-seconds (120 s by default), split over the steps
+    budget = max(0.05, 8.0 * args.cpu_seconds / max(1, args.steps + args.warmup))
     count = int(max(threads, budget / max(per_a, 1e-9)))
     times = []
     for s in range(args.warmup + args.steps):
@@ -279,14 +296,11 @@ def main():
     launches = ctx.launch_count() - launches0
     step_ms = [a.elapsed_time(b) for a, b in ev]
     t_local = sum(step_ms) / 1e3
-    t = torch.tensor([t_local], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    t_max = float(t.item())
+    t_max = max_over_ranks(t_local, world, dev)
     strings_per_step = 4.0 ** N if args.xstrings <= 0 else float(args.xstrings) * 2 ** N
     if args.xstrings > 0:
         M = ln = None
-    value = world * args.steps * strings_per_step / t_max
+    value = aggregate_rate(world, args.steps, strings_per_step, t_max)
     clocks = clk.summary()
 
     # end-to-end: the C-ABI host-buffer call, H2D copy from pinned memory inside the timed region
@@ -299,10 +313,8 @@ def main():
         for _ in range(args.steps):
             hm.sre_host(host.numpy(), 2.0, device=local)
         barrier()
-        te = torch.tensor([time.perf_counter() - t0], dtype=torch.float64, device=dev)
-        if world > 1:
-            dist.all_reduce(te, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * args.steps * strings_per_step / float(te.item()), "unit": UNIT,
+        te = max_over_ranks(time.perf_counter() - t0, world, dev)
+        e2e = {"value": aggregate_rate(world, args.steps, strings_per_step, te), "unit": UNIT,
                "h2d_bytes_per_step": int(psi_np.nbytes), "d2h_bytes_per_step": 3 * 8 + 4}
 
     line = None
