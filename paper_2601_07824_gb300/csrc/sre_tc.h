@@ -12,10 +12,9 @@ struct TcParams {
     int64_t count;           // number of X-strings
     const int64_t* a_list;   // nullptr: a = 0 .. count-1; else a = a_list[i] (checked in range)
     int per_a;               // 1: per-X-string triples out[count][2^(N-14) tiles][8 warps][3]; 0: per-CTA
-    float* scratch;          // R slots x A X-strings x 2^N floats (re plane, im plane)
-    int R, A;
-    int64_t n_batches;
-    int p1, p2;              // pass-1 / pass-2 tasks per batch (A * 2^(N-14) each)
+    float* scratch;          // R slots x 2^N floats (re plane, im plane of one X-string)
+    int R;                   // scratch slots, >= 3 (pass 2 runs two batches behind pass 1)
+    int64_t n_batches;       // one X-string per batch, 2^(N-14) tiles per pass
     unsigned* done1;         // per slot, monotonic
     unsigned* done2;
     int* status;

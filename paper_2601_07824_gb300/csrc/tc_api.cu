@@ -31,14 +31,11 @@ hadamag_status run_sre_tensor(hadamag_ctx_t c, const float2* psi, int N, double 
 
     TcParams P{};
     P.psi = ps; P.N = N; P.nq = n; P.count = count; P.a_list = a_list; P.per_a = per_a;
-    P.A = 1;
     // scratch of one X-string: 2^N floats (8 MiB at N = 21); pass 2 runs two batches behind
     // pass 1, so three slots are live at once
     P.R = N <= 22 ? 4 : 3;
     P.n_batches = count;
-    P.p1 = tc_tiles_per_a(N);
-    P.p2 = tc_tiles_per_a(N);
-    const size_t scratch_bytes = (size_t)P.R * P.A * ((size_t)1 << N) * sizeof(float);
+    const size_t scratch_bytes = (size_t)P.R * ((size_t)1 << N) * sizeof(float);
     if ((s = ensure_buf(c, c->scratch, scratch_bytes))) return s;
     if ((s = ensure_buf(c, c->counters, 2 * 64 * sizeof(unsigned)))) return s;
     P.scratch = (float*)c->scratch.ptr;
@@ -50,7 +47,7 @@ hadamag_status run_sre_tensor(hadamag_ctx_t c, const float2* psi, int N, double 
     P.scale_exp = fexp;
     int grid = 0;
     if ((e = tc_max_grid(N, mode, c->sm_count, &grid)) != cudaSuccess) return cuda_fail(c, e, "tc occupancy");
-    const int64_t total = (P.n_batches + 2) * (int64_t)P.p1;  // work items (pass-1 + pass-2 tile pairs)
+    const int64_t total = (P.n_batches + 2) * (int64_t)tc_tiles_per_a(N);  // work items
     if (grid > total) grid = (int)total;
     const int tiles = tc_triples_per_a(N);
     if (per_a) {
