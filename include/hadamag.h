@@ -33,7 +33,7 @@ extern "C" {
 typedef enum {
     HADAMAG_OK = 0,
     HADAMAG_ERR_INVALID_ARG = 1, /* bad N, n, count, null or misaligned pointer, bad list entry */
-    HADAMAG_ERR_UNSUPPORTED = 2, /* valid request outside what this build implements */
+    HADAMAG_ERR_UNSUPPORTED = 2, /* valid request outside what the library implements */
     HADAMAG_ERR_OOM = 3,         /* device or pinned allocation failed */
     HADAMAG_ERR_CUDA = 4,        /* a CUDA runtime call failed (see hadamag_last_error) */
     HADAMAG_ERR_TIMEOUT = 5,     /* a bounded inter-CTA wait ran out; the launch stopped early */
@@ -158,7 +158,7 @@ hadamag_status hadamag_sre_grad(hadamag_ctx_t ctx, const void* psi_dev, int N, h
 
 /*
  * Many states of uneven N (10 <= N_i <= 18, complex64) in ONE persistent launch (the batched
- * form of configs[3]; not in the paper): M_2 of state i into M2_dev[i] (device doubles) and, if
+ * form for many states of uneven N; not in the paper): M_2 of state i into M2_dev[i] (device doubles) and, if
  * want_grad, dM_2/dpsi* into grad_dev[i] (complex64).  psi_dev and grad_dev are HOST arrays of
  * `count` device pointers.  States with N <= 14 are one CTA item each; larger states run the
  * three-pass adjoint; the work list is ordered largest first and taken through a dynamic

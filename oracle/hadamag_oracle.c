@@ -17,7 +17,7 @@
  *     m += sum_b |chi_b|;  mana = log2(m / 3^N).
  *   - lost_norm = 1 - sum_P <P>^2 / 2^N (Sec. 4.1, Eq. distNAT).
  *
- * Readings where the paper is silent or garbled (each also listed in the design doc):
+ * Readings where the paper is silent or garbled:
  *   R1  Algorithm 2 accumulates chi_b^{2q}; X_a Z_b is anti-Hermitian when a.b is odd, so
  *       chi_b is then imaginary.  Eq. (sre) uses Hermitian Pauli strings (real <P>), so the
  *       accumulated term is |chi_b|^{2q}.

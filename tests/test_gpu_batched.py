@@ -1,4 +1,4 @@
-"""Batched persistent launch (configs[3]): 64 states, N_i ~ U{10..18}, RY/RZ + CZ-ladder
+"""Batched persistent launch: 64 states, N_i ~ U{10..18}, RY/RZ + CZ-ladder
 circuits of depth 8, M_2 and dM_2/dpsi* in one launch.  Checked against the single-state
 adjoint (itself checked against the oracle), the FP64 oracle on the small states, FP64
 finite differences (step 1e-4), and a CUDA-graph capture + replay."""

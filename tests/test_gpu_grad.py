@@ -49,8 +49,8 @@ def test_grad_unnormalised_complex128_vs_oracle():
 
 
 @pytest.mark.parametrize("N", [10, 12])
-def test_config4_finite_differences(N):
-    # config-4 style state (RY/RZ + CZ ladder, depth 8); central FD in FP64 with step 1e-4
+def test_batched_ladder_states_finite_differences(N):
+    # RY/RZ + CZ-ladder state (depth 8, random angles); central FD in FP64 with step 1e-4
     rng = np.random.default_rng(4001 + N)
     psi = I.ry_rz_cz_ladder(N, 8, rng, dtype=np.complex128)
     _, g = hm.sre_grad(on_dev(psi))

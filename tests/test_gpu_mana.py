@@ -41,7 +41,7 @@ def test_gaussian_vs_oracle(N):
     assert abs(sw - swo) <= 1e-6 * swo
 
 
-def test_config3_N11_and_strange_closed_form(golden):
+def test_N11_gaussian_and_strange_closed_form(golden):
     psi = I.gaussian_state(11, 1101, d=3, dtype=np.complex64)
     m, sw = hm.mana(on_dev(psi))
     # additivity-free check at full size: sum|W| >= sum W = 1 and the Haar-typical magnitude

@@ -1,4 +1,4 @@
-"""Uniform-X Monte-Carlo M_2 (configs[4] second leg) on the GPU: bit-exact X-strings, per-sample
+"""Uniform-X Monte-Carlo M_2 (N = 28, 4096 sampled X-strings, and smaller cases) on the GPU: bit-exact X-strings, per-sample
 sums against the FP64 oracle (including the three-pass HBM schedule at N = 25 and 28), and the
 estimator against the exact value / Haar band.  Per-sample tolerance 2e-5 relative."""
 import numpy as np
@@ -44,7 +44,7 @@ def test_hbm_schedule_terms_vs_oracle(N):
     np.testing.assert_allclose(got[:, 0], want, rtol=2e-5)
 
 
-def test_config5_mc_N28():
+def test_mc_N28_4096_samples():
     N, samples = 28, 4096
     psi = I.gaussian_state(N, 2801, dtype=np.complex64)
     t = on_dev(psi)

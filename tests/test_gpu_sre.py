@@ -41,7 +41,7 @@ def test_onepass_sweep_vs_oracle(N):
         assert abs(ln - lno) < 1e-6
 
 
-def test_config1_complex128_closed_forms(golden):
+def test_N12_complex128_closed_forms(golden):
     g = golden["closed_forms"]["sre_t_state_per_qubit"]
     t = on_dev(I.t_state_product(12))
     for n, key in ((1.0, "M1"), (2.0, "M2"), (3.0, "M3")):
@@ -54,7 +54,7 @@ def test_config1_complex128_closed_forms(golden):
         assert abs(M) < 1e-6
 
 
-def test_config1_gaussian_complex128_vs_oracle():
+def test_N12_gaussian_complex128_vs_oracle():
     psi = I.gaussian_state(12, 1201)  # complex128 input
     t = on_dev(psi)
     for n in (1.0, 2.0, 3.0):
@@ -112,7 +112,7 @@ def test_twopass_sampled_terms_and_exact_identities(N):
         assert 0.0 < M < N
 
 
-def test_config2_brickwork_N20_total_equals_sum_of_terms():
+def test_brickwork_N20_total_equals_sum_of_terms():
     psi = I.brickwork_haar(20, 10, seed=2001)  # complex64
     t = on_dev(psi)
     M, ln = hm.sre(t, 2.0)
