@@ -14,14 +14,16 @@
 // of two 2^f (chosen from max|psi|^2) so that every fp16 operand stays in range; the per-CTA
 // FP64 sums are unscaled exactly at the end.  FP64 is used only for the cross-tile sums.
 //
-// Schedule: one CTA per SM; each work item pairs a pass-1 tile of X-string batch s with a
-// pass-2 tile of batch s - 2, and interleaves their phases so that every MMA runs while the
-// threads work on the other tile:
-//   produce(P) -> MMA1(P) | load(Q) -> MMA3(Q) | convert(P) -> MMA2(P) | reduce(Q) | store(P).
-// The pair-product inputs of pass 1 (two 8 KiB state rows per eighth of a tile) arrive by bulk
-// asynchronous copies into four staging buffers, issued two eighths ahead (and across work
-// items), so the producer reads shared memory only.  The pass-2 tile of the next item is
-// loaded into registers at the end of the current one.
+// Schedule: one CTA of 512 threads per SM, split into two independent groups of 256 threads
+// (warps 0-7 and 8-15) with their own named barriers, mbarriers and inter-CTA waits:
+//   pass-1 group: staged pair products -> MMA1 -> block-1/block-2 conversion -> MMA2;
+//   pass-2 group: scratch -> register butterflies -> MMA3 -> reduction, then the store of the
+//                 block-2 result of the matching pass-1 tile to scratch.
+// Block 2 has its own tensor-memory columns, handed over by two mbarriers ("full" from the
+// MMA2 commit, "free" once the pass-2 group has read it), so the pass-1 group never waits on
+// another CTA.  The pair-product inputs of pass 1 (two 8 KiB state rows per eighth of a tile)
+// arrive by bulk asynchronous copies into four staging buffers, issued two eighths ahead (and
+// across tiles), so the producer reads shared memory only.
 #include "common.cuh"
 #include "pairs.cuh"
 #include "sre_tc.h"
@@ -186,9 +188,10 @@ struct P1Item {
 }  // namespace
 
 // ------------------------------------------------------------------------------------------
-// Persistent kernel, 256 threads, one CTA per SM, static round-robin over work items.  Work
+// Persistent kernel, 512 threads, one CTA per SM, static round-robin over work items.  Work
 // item c: stage s = c / T, tile r = c % T (T = 2^M tiles per X-string, one X-string per batch);
-// pass-1 tile r of batch s (s < n_batches) and pass-2 tile r of batch s - 2 (s >= 2).  R
+// the pass-1 group does pass-1 tile r of batch s (s < n_batches), the pass-2 group pass-2
+// tile r of batch s - 2 (s >= 2) and the scratch store of pass-1 tile r of batch s.  R
 // scratch slots; batch g uses slot g % R (R >= 3).
 // Scratch of one X-string: floats [re/im][h = z' >> 13][q][n][m' & 3] with z' & 8191 =
 // (m' << 7) | n and q = m' >> 2 (pass 1 writes 16-byte rows, pass 2 reads 32-byte runs).
@@ -564,7 +567,7 @@ static cudaError_t tc_prep(int* occ) {
     auto k = sre_tc<MODE, RB>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)SM_DYN);
     if (e != cudaSuccess) return e;
-    // two CTAs of ~97 KiB per SM need the largest shared-memory carveout
+    // one CTA with 225 KiB of shared memory needs the largest shared-memory carveout
     e = cudaFuncSetAttribute(k, cudaFuncAttributePreferredSharedMemoryCarveout, (int)cudaSharedmemCarveoutMaxShared);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, 512, SM_DYN);
