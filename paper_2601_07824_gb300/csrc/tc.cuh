@@ -1,10 +1,11 @@
 // tc.cuh -- tcgen05 (5th-generation tensor core) primitives for sm_103a, inline PTX.
 //
-// Operands live in shared memory in the no-swizzle canonical layout: "core matrices" of
-// 8 rows x 16 bytes (8 fp16 values), each 128 contiguous bytes.  A K-major operand holds 8
-// consecutive K values of one row in a 16-byte core-matrix row; an MN-major operand holds 8
-// consecutive rows (M or N index) of one K value.  The matrix descriptor carries the byte
-// distance between core matrices adjacent along K (LBO) and along M/N (SBO).
+// Operands live in shared memory, either in the no-swizzle canonical layout -- "core
+// matrices" of 8 rows x 16 bytes (8 fp16 values), each 128 contiguous bytes; a K-major operand
+// holds 8 consecutive K values of one row in a 16-byte core-matrix row, an MN-major operand 8
+// consecutive rows (M or N index) of one K value; the matrix descriptor carries the byte
+// distance between core matrices adjacent along K (LBO) and along M/N (SBO) -- or in the
+// 128-byte-swizzle layout described at sdesc().
 // The accumulator is fp32 in tensor memory (TMEM): row i of D in lane i, column j in column j.
 #pragma once
 #include <cuda_fp16.h>
