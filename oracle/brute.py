@@ -97,3 +97,21 @@ def mana_brute(psi: np.ndarray):
     W = wigner_brute(psi)
     s = float(np.abs(W.real).sum())
     return float(np.log2(s)), s
+
+
+def wigner_mixed_brute(rho: np.ndarray) -> np.ndarray:
+    """W(u) = tr(A_u rho)/3^N for a qutrit density matrix (site j = digit j), in the order of
+    `phase_point_operators`."""
+    rho = np.asarray(rho, dtype=np.complex128)
+    N = 0
+    while 3 ** N < rho.shape[0]:
+        N += 1
+    As, _ = phase_point_operators(N)
+    return np.array([np.trace(A @ rho) for A in As]) / 3 ** N
+
+
+def mana_mixed_brute(rho: np.ndarray):
+    """(mana in bits, sum |W|) of a qutrit density matrix from Eq. (mana)."""
+    W = wigner_mixed_brute(rho)
+    s = float(np.abs(W).sum())
+    return float(np.log2(s)), s
