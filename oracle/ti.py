@@ -1,0 +1,116 @@
+"""Thermodynamic-integration estimate of M_2 (Sec. 3.2, Eqs. Boltz to M2_TI, Algorithm 3),
+FP64 NumPy.  TEST INFRASTRUCTURE ONLY: only `tests/` may import this module.
+
+The X-strings a are sampled from Pi_beta(a) = exp(-beta f(a)) / Z_beta with the "energy"
+f(a) = -ln(S(a) + eps), S(a) = sum_b |<psi|X_a Z_b|psi>|^4 (the per-X-string sum of
+Algorithm 2, taken from the FP64 oracle), and
+    <f>_beta = -d ln Z_beta / d beta,  Z_0 = 2^N,  Z_1 = S_2 + 2^N eps.
+
+Readings (the printed text is inconsistent here):
+  * Sign.  Integrating <f>_beta = -d ln Z / d beta over [0, 1] gives ln Z_0 - ln Z_1, so
+    I = int_0^1 <f>_beta d beta = -ln((S_2 + 2^N eps) / 2^N) and
+    M_2 = -log2(exp(-I) - eps)  (eps = 0: M_2 = I / ln 2).
+    The printed identity (ln Z_1 - ln Z_0) and Algorithm 3's return value (-1/ln 2 times the
+    quadrature) carry the opposite sign; as printed they give M_2 <= 0.
+  * Natural log in f: Z_1 = sum_a exp(-f(a)) = S_2 requires f = -ln S, not -log2 S.
+  * Quadrature: composite Simpson on L points beta_l = l / (L - 1).  Algorithm 3 asks for an
+    even L, which gives an odd number of intervals; for even L the last three intervals use
+    Simpson's 3/8 rule.
+  * Random numbers: each chain l draws from SplitMix64 (the generator of the uniform-X
+    estimator) seeded with seed + l; per step one output picks the bit to flip (the local,
+    symmetric proposal: one uniformly chosen bit of a) and one output, as a double in [0, 1)
+    from its top 53 bits, decides acceptance; the start pattern is the top N bits of the
+    chain's first output.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def energies(psi, eps: float = 0.0) -> np.ndarray:
+    """f(a) = -ln(S(a) + eps) for every X-string a (S(a) from the FP64 oracle)."""
+    import oracle
+    Sq, _, _ = oracle.sre_terms(psi, 2.0)
+    S = Sq + eps
+    if np.any(S <= 0.0):
+        raise ValueError("S(a) + eps must be positive for every a (use eps > 0)")
+    return -np.log(S)
+
+
+def boltzmann_mean(f: np.ndarray, beta: float) -> float:
+    """<f>_beta = sum_a Pi_beta(a) f(a), Eq. f_expect_beta_reg, by enumeration over all a."""
+    x = -beta * f
+    w = np.exp(x - x.max())
+    return float(np.sum(w * f) / np.sum(w))
+
+
+def simpson_weights(L: int) -> np.ndarray:
+    """Weights of composite Simpson's rule on L equally spaced points of [0, 1] (L >= 3); for
+    even L the last three intervals use the 3/8 rule."""
+    if L < 3:
+        raise ValueError("L >= 3")
+    h = 1.0 / (L - 1)
+    w = np.zeros(L)
+    n13 = L - 1 if L % 2 == 1 else L - 4  # intervals covered by the 1/3 rule
+    for i in range(0, n13, 2):
+        w[i] += h / 3.0
+        w[i + 1] += 4.0 * h / 3.0
+        w[i + 2] += h / 3.0
+    if L % 2 == 0:
+        i = L - 4
+        w[i] += 3.0 * h / 8.0
+        w[i + 1] += 9.0 * h / 8.0
+        w[i + 2] += 9.0 * h / 8.0
+        w[i + 3] += 3.0 * h / 8.0
+    return w
+
+
+def m2_from_integral(I: float, eps: float = 0.0) -> float:
+    """M_2 = -log2(exp(-I) - eps) (Eq. M2_TI_reg_explicit_correct with the sign reading)."""
+    return -math.log2(math.exp(-I) - eps)
+
+
+def m2_ti_exact(psi, L: int, eps: float = 0.0) -> float:
+    """Thermodynamic integration with the exact integrand <f>_beta (quadrature error only)."""
+    f = energies(psi, eps)
+    betas = np.linspace(0.0, 1.0, L)
+    I = float(np.dot(simpson_weights(L), [boltzmann_mean(f, b) for b in betas]))
+    return m2_from_integral(I, eps)
+
+
+def metropolis_means(f: np.ndarray, N: int, L: int, n_s: int, seed: int, burn_in: int = 0):
+    """Algorithm 3's chains: per beta_l, n_s Metropolis steps (one-bit flips, acceptance
+    min(1, exp(-beta (f' - f)))) after `burn_in` unrecorded ones; returns (means, visits)
+    with visits[l][a] = how often the recorded chain state was a."""
+    import oracle
+    betas = np.linspace(0.0, 1.0, L)
+    means = np.zeros(L)
+    visits = np.zeros((L, f.size), dtype=np.int64)
+    for l, beta in enumerate(betas):
+        steps = burn_in + n_s
+        r = oracle.splitmix64(seed + l, 1 + 2 * steps)
+        a = int(r[0] >> np.uint64(64 - N)) if N > 0 else 0
+        fa = f[a]
+        acc = 0.0
+        for t in range(steps):
+            bit = int(r[1 + 2 * t] % np.uint64(N))
+            u = float(r[2 + 2 * t] >> np.uint64(11)) * 2.0 ** -53
+            a2 = a ^ (1 << bit)
+            f2 = f[a2]
+            if u < math.exp(min(0.0, -beta * (f2 - fa))):
+                a, fa = a2, f2
+            if t >= burn_in:
+                acc += fa
+                visits[l, a] += 1
+        means[l] = acc / n_s
+    return means, visits
+
+
+def m2_metropolis(psi, L: int, n_s: int, seed: int, burn_in: int = 0, eps: float = 0.0) -> float:
+    """Algorithm 3 (with the sign reading): M_2 estimate from L chains of n_s samples."""
+    f = energies(psi, eps)
+    N = int(round(math.log2(f.size)))
+    means, _ = metropolis_means(f, N, L, n_s, seed, burn_in)
+    return m2_from_integral(float(np.dot(simpson_weights(L), means)), eps)

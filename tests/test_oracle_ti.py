@@ -1,0 +1,100 @@
+"""Pins of the thermodynamic-integration M_2 oracle (Sec. 3.2, Algorithm 3) on the CPU.
+
+Against things other than the estimator itself: the exact M_2 of the FP64 oracle (the
+identity with the exact integrand converges at Simpson's fourth order), polynomial exactness
+of the quadrature weights, the defining relation <f>_beta = -d ln Z / d beta by finite
+differences, closed forms with eps > 0 on a stabilizer state, the stationary distribution of
+the Metropolis chains (visit frequencies against Pi_beta), and planted mistakes (the printed
+sign, log2 in the energy, an inverted acceptance rule) that must fail."""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import ti
+from paper_2601_07824_gb300 import inputs as I
+
+
+@pytest.mark.parametrize("L", [3, 5, 9, 4, 6, 10])
+def test_simpson_weights_integrate_cubics_exactly(L):
+    w = ti.simpson_weights(L)
+    x = np.linspace(0.0, 1.0, L)
+    for k in range(4):
+        assert np.dot(w, x ** k) == pytest.approx(1.0 / (k + 1), abs=1e-14)
+
+
+def test_boltzmann_mean_is_minus_dlnZ_dbeta():
+    f = ti.energies(I.gaussian_state(5, 3))
+    lnZ = lambda b: float(np.log(np.sum(np.exp(-b * f))))  # noqa: E731
+    for beta in (0.0, 0.3, 0.8, 1.0):
+        h = 1e-5
+        assert ti.boltzmann_mean(f, beta) == pytest.approx(-(lnZ(beta + h) - lnZ(beta - h)) / (2 * h), rel=1e-7)
+    # beta = 0: the plain mean; beta = 1: Z_1 = S_2 (natural log in f)
+    assert ti.boltzmann_mean(f, 0.0) == pytest.approx(f.mean(), rel=1e-13)
+    S2 = oracle.sre_terms(I.gaussian_state(5, 3), 2.0)[0].sum()
+    assert np.sum(np.exp(-f)) == pytest.approx(S2, rel=1e-12)
+
+
+@pytest.mark.parametrize("state", ["gauss", "brick", "tprod"])
+def test_exact_integrand_converges_to_exact_m2(state):
+    psi = {"gauss": I.gaussian_state(7, 21), "brick": I.brickwork_haar(8, 6, seed=3, dtype=np.complex128),
+           "tprod": I.t_state_product(6)}[state]
+    M2 = oracle.sre(psi, 2.0)[0]
+    e17 = abs(ti.m2_ti_exact(psi, 17) - M2)
+    e33 = abs(ti.m2_ti_exact(psi, 33) - M2)
+    assert e33 < 2e-6 * max(1.0, M2)
+    assert e33 < e17 / 6  # fourth order: halving the step divides the error by ~16
+    assert ti.m2_ti_exact(psi, 32) == pytest.approx(M2, abs=5e-6 * max(1.0, M2))  # even L: 3/8 end panel
+
+
+def test_eps_regularisation_on_a_stabilizer_state():
+    # |0...0>: S(a) = 0 for a != 0, so eps > 0 is required; M_2 = -log2(exp(-I) - eps) = 0
+    z = I.zero_state(6)
+    with pytest.raises(ValueError):
+        ti.energies(z)
+    for eps in (1e-3, 1e-1):
+        assert abs(ti.m2_ti_exact(z, 65, eps=eps)) < 1e-6
+    # the identity Z_1 = S_2 + 2^N eps
+    f = ti.energies(z, eps=1e-3)
+    assert np.sum(np.exp(-f)) == pytest.approx(2 ** 6 + 2 ** 6 * 1e-3, rel=1e-12)
+
+
+def test_metropolis_chains_sample_the_boltzmann_distribution():
+    f = ti.energies(I.gaussian_state(5, 4))
+    means, visits = ti.metropolis_means(f, 5, 3, 200000, seed=77, burn_in=1000)
+    for l, beta in enumerate((0.0, 0.5, 1.0)):
+        p = np.exp(-beta * f)
+        p /= p.sum()
+        emp = visits[l] / visits[l].sum()
+        assert 0.5 * np.abs(emp - p).sum() < 0.03, beta
+        assert means[l] == pytest.approx(ti.boltzmann_mean(f, beta), rel=0.03)
+
+
+def test_metropolis_estimate_and_reproducibility():
+    psi = I.gaussian_state(6, 9)
+    M2 = oracle.sre(psi, 2.0)[0]
+    for seed in (0, 100, 200):
+        assert ti.m2_metropolis(psi, 9, 20000, seed, burn_in=500) == pytest.approx(M2, rel=0.02)
+    assert ti.m2_metropolis(psi, 5, 500, 7) == ti.m2_metropolis(psi, 5, 500, 7)  # seeded, deterministic
+
+
+def test_planted_mistakes_fail():
+    psi = I.gaussian_state(7, 21)
+    M2 = oracle.sre(psi, 2.0)[0]
+    f = ti.energies(psi)
+    betas = np.linspace(0.0, 1.0, 33)
+    I_ = float(np.dot(ti.simpson_weights(33), [ti.boltzmann_mean(f, b) for b in betas]))
+    # the printed return value of Algorithm 3 (-1/ln 2 times the quadrature) is -M_2
+    assert -I_ / math.log(2.0) == pytest.approx(-M2, rel=1e-5)
+    assert abs(-I_ / math.log(2.0) - M2) > 1.0
+    # log2 instead of ln in the energy breaks Z_1 = S_2
+    f2 = f / math.log(2.0)
+    I2 = float(np.dot(ti.simpson_weights(33), [ti.boltzmann_mean(f2, b) for b in betas]))
+    assert abs(ti.m2_from_integral(I2) - M2) > 0.1
+    # an inverted acceptance rule (min(1, exp(+beta df))) samples the wrong distribution
+    g = ti.energies(I.gaussian_state(5, 4))
+    _, visits = ti.metropolis_means(-g, 5, 3, 50000, seed=77, burn_in=500)
+    p = np.exp(-1.0 * g)
+    p /= p.sum()
+    assert 0.5 * np.abs(visits[2] / visits[2].sum() - p).sum() > 0.1
