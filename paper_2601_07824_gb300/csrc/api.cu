@@ -109,50 +109,6 @@ TwoPlan plan_twopass(int N) {
     return p;
 }
 
-// Warp-specialised kernel for 16 <= N <= 20 (one CTA per SM).
-hadamag_status run_sre_ws(hadamag_ctx_t c, const float2* psi, int N, double n, int64_t count,
-                          const int64_t* a_list, int per_a, double* terms, cudaStream_t st, int64_t* nparts) {
-    hadamag_status s;
-    cudaError_t e;
-    const int L = N - 1, M = N - 11;
-    const size_t per_x = ((size_t)1 << L) * sizeof(float2);
-    int A = 8;
-    while (A > 1 && (size_t)A * per_x > ((size_t)16 << 20)) A >>= 1;
-    WsParams P{};
-    P.psi = psi; P.N = N; P.nq = n; P.count = count; P.a_list = a_list;
-    P.R = 4; P.A = A;
-    P.n_batches = (count + A - 1) / A;
-    P.p1 = A * (1 << M) / 2;
-    const int tiles = ws_tiles_per_a(N);
-    P.p2 = A * tiles;
-    int grid = c->sm_count;
-    if ((s = ensure_buf(c, c->scratch, (size_t)P.R * A * per_x))) return s;
-    if ((s = ensure_buf(c, c->counters, 2 * 64 * sizeof(unsigned)))) return s;
-    P.scratch = (float2*)c->scratch.ptr;
-    P.done1 = (unsigned*)c->counters.ptr; P.done2 = P.done1 + 64;
-    P.status = (int*)c->status.ptr; P.spin_limit = c->spin_limit; P.wait_bias = c->wait_bias;
-    P.per_a = per_a;
-    if (per_a) {
-        if ((s = ensure_buf(c, c->tiles, (size_t)count * tiles * 3 * sizeof(double)))) return s;
-        P.out = (double*)c->tiles.ptr;
-    } else {
-        if ((s = ensure_buf(c, c->part, (size_t)grid * 3 * sizeof(double)))) return s;
-        P.out = (double*)c->part.ptr;
-    }
-    if ((e = cudaMemsetAsync(c->counters.ptr, 0, 2 * 64 * sizeof(unsigned), st)) != cudaSuccess)
-        return cuda_fail(c, e, "memset counters");
-    e = launch_ws(P, sre_mode(n), grid, st);
-    c->launches++;
-    if (e != cudaSuccess) return cuda_fail(c, e, "sre_ws");
-    if (per_a) {
-        e = launch_sum_tiles((double*)c->tiles.ptr, count, tiles, terms, st);
-        c->launches++;
-        if (e != cudaSuccess) return cuda_fail(c, e, "sum_tiles");
-    }
-    if (nparts) *nparts = grid;
-    return HADAMAG_OK;
-}
-
 // Runs Algorithm 2 over `count` X-strings (all of them when a_list is null).  per_a = 0:
 // per-CTA partial triples go to c->part and *nparts receives their number.  per_a = 1:
 // per-X-string triples are written to terms (device).
@@ -180,7 +136,6 @@ hadamag_status run_sre(hadamag_ctx_t c, const float2* psi, int N, double n, int6
         return HADAMAG_OK;
     }
     if (N > 24) return fail(c, HADAMAG_ERR_UNSUPPORTED, "exact SRE supports N <= 24 (got %d)", N);
-    if (N <= 20 && c->sre_kernel == 1) return run_sre_ws(c, psi, N, n, count, a_list, per_a, terms, st, nparts);
     TwoPlan pl = plan_twopass(N);
     int grid = 0;
     if ((e = twopass_max_grid(N, mode, c->sm_count, &grid)) != cudaSuccess) return cuda_fail(c, e, "occupancy");
@@ -259,7 +214,6 @@ extern "C" hadamag_status hadamag_create(hadamag_ctx_t* out, int device) {
     hadamag_ctx_t c = new (std::nothrow) hadamag_ctx_s();
     if (!c) return HADAMAG_ERR_OOM;
     c->device = device;
-    if (const char* k = getenv("HADAMAG_SRE_KERNEL")) c->sre_kernel = (strcmp(k, "ws") == 0) ? 1 : 0;
     cudaError_t e = cudaSetDevice(device);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->sm_count, cudaDevAttrMultiProcessorCount, device);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&c->own_stream, cudaStreamNonBlocking);

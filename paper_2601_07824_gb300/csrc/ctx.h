@@ -37,7 +37,6 @@ struct hadamag_ctx_s {
     int autotune = 1;
     void* host_table = nullptr;  // pinned copy of the batched state table
     size_t host_table_bytes = 0;
-    int sre_kernel = 0;  // 16 <= N <= 20: 0 = two-pass, 1 = warp-specialised (HADAMAG_SRE_KERNEL=ws)
     uint64_t launches = 0;
     char last_error[256] = {0};
     std::vector<hm::DevBuf*> all_bufs() {
@@ -56,8 +55,6 @@ hadamag_status as_c64(hadamag_ctx_t c, const void* psi, int64_t n, hadamag_dtype
                       const float2** out);
 int sre_mode(double n);
 TwoPlan plan_twopass(int N);
-hadamag_status run_sre_ws(hadamag_ctx_t c, const float2* psi, int N, double n, int64_t count,
-                          const int64_t* a_list, int per_a, double* terms, cudaStream_t st, int64_t* nparts);
 hadamag_status run_sre(hadamag_ctx_t c, const float2* psi, int N, double n, int64_t count,
                        const int64_t* a_list, int per_a, double* terms, cudaStream_t st, int64_t* nparts);
 hadamag_status begin(hadamag_ctx_t c, cudaStream_t st);

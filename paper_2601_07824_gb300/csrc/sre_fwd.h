@@ -45,28 +45,6 @@ struct TwoPassParams {
     int per_a;
 };
 
-// Warp-specialised persistent kernel (16 <= N <= 20): pass-1 warps and a pass-2 group per SM.
-struct WsParams {
-    const float2* psi;
-    int N;
-    double nq;
-    int64_t count;
-    const int64_t* a_list;
-    float2* scratch;         // R slots x A X-strings x 2^(N-1) values
-    int R, A;
-    int64_t n_batches;
-    int p1, p2;              // pass-1 warp tasks / pass-2 tiles per batch
-    unsigned* done1;
-    unsigned* done2;
-    int* status;
-    long long spin_limit;
-    unsigned wait_bias;
-    double* out;
-    int per_a;
-};
-int ws_tiles_per_a(int N);
-cudaError_t launch_ws(const WsParams& P, int mode, int grid, cudaStream_t st);
-
 // Three-pass per-X-string kernel for 25 <= N <= 28 (scratch in HBM), one X-string per batch.
 struct HbmParams {
     const float2* psi;
