@@ -8,6 +8,9 @@
 //     order, runtime dispatch on M = N - 11), scattering into per-CTA partial gradients shared by
 //     all large states, followed by finalize tasks that reduce those partials (FP64, fixed CTA
 //     order), write the gradient, zero the partials and release them to the next large state.
+// Forward only (no gradient requested): small states skip the cube, the back transform and the
+// scatter; large states run passes 1 and 2 only, and one finalize task per state turns the
+// pass-2 sums into M_2 once every pass-2 task has counted in.  No partial-gradient buffers.
 // Every wait is on a task with a smaller ticket, which a running CTA already holds, so the
 // launch cannot deadlock (waits are bounded and report a timeout through the status word).
 // Assignment of tasks to CTAs is dynamic, so sums may differ between runs in the last bits.
