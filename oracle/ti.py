@@ -39,6 +39,24 @@ def energies(psi, eps: float = 0.0) -> np.ndarray:
     return -np.log(S)
 
 
+def energy_fn(psi, eps: float = 0.0):
+    """f(a) = -ln(S(a) + eps) evaluated on demand, one X-string at a time, and cached: the
+    chains visit a small part of the 2^N X-strings, so this is what makes N >= 14 cheap.
+    Raises ValueError when an evaluated S(a) + eps is not positive."""
+    import oracle
+    cache = {}
+
+    def f(a: int) -> float:
+        v = cache.get(a)
+        if v is None:
+            S = float(oracle.sre_terms_list(psi, [a])[0]) + eps
+            if S <= 0.0:
+                raise ValueError("S(a) + eps must be positive for every visited a (use eps > 0)")
+            v = cache[a] = -math.log(S)
+        return v
+    return f
+
+
 def boltzmann_mean(f: np.ndarray, beta: float) -> float:
     """<f>_beta = sum_a Pi_beta(a) f(a), Eq. f_expect_beta_reg, by enumeration over all a."""
     x = -beta * f
@@ -80,37 +98,54 @@ def m2_ti_exact(psi, L: int, eps: float = 0.0) -> float:
     return m2_from_integral(I, eps)
 
 
-def metropolis_means(f: np.ndarray, N: int, L: int, n_s: int, seed: int, burn_in: int = 0):
+def metropolis_means(f, N: int, L: int, n_s: int, seed: int, burn_in: int = 0, record: dict | None = None):
     """Algorithm 3's chains: per beta_l, n_s Metropolis steps (one-bit flips, acceptance
     min(1, exp(-beta (f' - f)))) after `burn_in` unrecorded ones; returns (means, visits)
-    with visits[l][a] = how often the recorded chain state was a."""
+    with visits[l][a] = how often the recorded chain state was a.
+
+    f is the energy table (f[a] for every a) or a callable a -> f(a).  With `record` given,
+    record["traj"][l, t] is the chain state after step t (burn-in included) and
+    record["margin"][l, t] = |u - p_acc| of that step's decision (how far the decision was
+    from going the other way)."""
     import oracle
+    energy = f if callable(f) else f.__getitem__
     betas = np.linspace(0.0, 1.0, L)
     means = np.zeros(L)
-    visits = np.zeros((L, f.size), dtype=np.int64)
+    visits = np.zeros((L, 1 << N), dtype=np.int64) if not callable(f) else None
+    steps = burn_in + n_s
+    if record is not None:
+        record["traj"] = np.zeros((L, steps), dtype=np.int64)
+        record["margin"] = np.zeros((L, steps))
     for l, beta in enumerate(betas):
-        steps = burn_in + n_s
         r = oracle.splitmix64(seed + l, 1 + 2 * steps)
         a = int(r[0] >> np.uint64(64 - N)) if N > 0 else 0
-        fa = f[a]
+        fa = energy(a)
         acc = 0.0
         for t in range(steps):
             bit = int(r[1 + 2 * t] % np.uint64(N))
             u = float(r[2 + 2 * t] >> np.uint64(11)) * 2.0 ** -53
             a2 = a ^ (1 << bit)
-            f2 = f[a2]
-            if u < math.exp(min(0.0, -beta * (f2 - fa))):
+            f2 = energy(a2)
+            p_acc = math.exp(min(0.0, -beta * (f2 - fa)))
+            if u < p_acc:
                 a, fa = a2, f2
+            if record is not None:
+                record["traj"][l, t] = a
+                record["margin"][l, t] = abs(u - p_acc)
             if t >= burn_in:
                 acc += fa
-                visits[l, a] += 1
+                if visits is not None:
+                    visits[l, a] += 1
         means[l] = acc / n_s
     return means, visits
 
 
-def m2_metropolis(psi, L: int, n_s: int, seed: int, burn_in: int = 0, eps: float = 0.0) -> float:
-    """Algorithm 3 (with the sign reading): M_2 estimate from L chains of n_s samples."""
-    f = energies(psi, eps)
-    N = int(round(math.log2(f.size)))
-    means, _ = metropolis_means(f, N, L, n_s, seed, burn_in)
+def m2_metropolis(psi, L: int, n_s: int, seed: int, burn_in: int = 0, eps: float = 0.0,
+                  record: dict | None = None) -> float:
+    """Algorithm 3 (with the sign reading): M_2 estimate from L chains of n_s samples.  Up to
+    12 qubits the energy table is built for every a; beyond, energies are evaluated on demand."""
+    psi = np.asarray(psi)
+    N = int(round(math.log2(psi.size)))
+    f = energies(psi, eps) if N <= 12 else energy_fn(psi, eps)
+    means, _ = metropolis_means(f, N, L, n_s, seed, burn_in, record)
     return m2_from_integral(float(np.dot(simpson_weights(L), means)), eps)

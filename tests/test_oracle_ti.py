@@ -98,3 +98,42 @@ def test_planted_mistakes_fail():
     p = np.exp(-1.0 * g)
     p /= p.sum()
     assert 0.5 * np.abs(visits[2] / visits[2].sum() - p).sum() > 0.1
+
+
+def test_energies_on_demand_give_the_same_chains():
+    # the cached per-X-string evaluation is the table's arithmetic, one X-string at a time
+    psi = I.gaussian_state(8, 13)
+    table = ti.energies(psi)
+    lazy = ti.energy_fn(psi)
+    for a in (0, 1, 77, 255):
+        assert lazy(a) == pytest.approx(table[a], rel=1e-14)
+    ra, rb = {}, {}
+    ma, _ = ti.metropolis_means(table, 8, 4, 300, seed=5, burn_in=20, record=ra)
+    mb, vb = ti.metropolis_means(lazy, 8, 4, 300, seed=5, burn_in=20, record=rb)
+    assert vb is None
+    np.testing.assert_array_equal(ra["traj"], rb["traj"])
+    np.testing.assert_allclose(ma, mb, rtol=1e-13)
+    with pytest.raises(ValueError):
+        ti.energy_fn(I.zero_state(4))(3)  # S(3) = 0 on |0000>
+
+
+def test_recorded_trajectory_is_a_valid_chain():
+    N, L, n_s, burn = 7, 5, 400, 30
+    psi = I.gaussian_state(N, 17)
+    f = ti.energies(psi)
+    rec = {}
+    means, visits = ti.metropolis_means(f, N, L, n_s, seed=11, burn_in=burn, record=rec)
+    traj, margin = rec["traj"], rec["margin"]
+    assert traj.shape == margin.shape == (L, burn + n_s)
+    assert np.all((margin >= 0.0) & (margin <= 1.0))
+    for l in range(L):
+        r = oracle.splitmix64(11 + l, 1 + 2 * (burn + n_s))
+        a = int(r[0] >> np.uint64(64 - N))
+        for t in range(burn + n_s):
+            flip = a ^ (1 << int(r[1 + 2 * t] % np.uint64(N)))
+            assert traj[l, t] in (a, flip)  # stay or take the proposed one-bit flip
+            a = int(traj[l, t])
+        assert means[l] == pytest.approx(f[traj[l, burn:]].mean(), rel=1e-12)
+        np.testing.assert_array_equal(np.bincount(traj[l, burn:], minlength=1 << N), visits[l])
+    # beta = 0 accepts every proposal
+    assert np.all(traj[0] != np.concatenate(([int(oracle.splitmix64(11, 1)[0] >> np.uint64(64 - N))], traj[0, :-1])))
