@@ -40,7 +40,8 @@ def parse():
     ap.add_argument("--path", default="cudacore", choices=["cudacore", "tensor", "auto"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--extra", action="store_true", help="also time N=22, mana N=11, MC N=28, batched")
+    ap.add_argument("--extra", action="store_true",
+                    help="also time N=22, mana N=11, MC N=28, batched, thermodynamic integration N=20")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--xstrings", type=int, default=0,
                     help="profiling aid: each step evaluates only the first K X-strings of the "
@@ -436,6 +437,17 @@ def extra_workloads(hm, dev, sm_count):
         dt, _ = timed(lambda: hm.sre_batched(ts, want_grad=True), reps=2)
         return {"strings_per_s": sum(4.0 ** n for n in Ns) / dt, "s": dt, "states": len(Ns)}
     guard("batched_64_fwd_bwd", batched)
+
+    # thermodynamic-integration M2 (Algorithm 3) on the N = 20 brickwork state: L = 10 chains,
+    # 200 burn-in + 2000 recorded steps, one per-X evaluation per chain and step
+    def ti20():
+        psi = torch.from_numpy(inputs.brickwork_haar(20, 10, seed=2001, dtype=np.complex64)).to(dev)
+        L, n_s, burn = 10, 2000, 200
+        dt, r = timed(lambda: hm.sre_ti(psi, L, n_s, 2002, burn_in=burn), warm=False)
+        evals = L * (n_s + burn + 1)
+        return {"strings_per_s": evals * 2.0 ** 20 / dt, "evaluations_per_s": evals / dt,
+                "steps_per_s": (n_s + burn) / dt, "s": dt, "M2": r[0], "L": L, "n_s": n_s, "burn_in": burn}
+    guard("ti_N20_L10", ti20)
     return out
 
 

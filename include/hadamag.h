@@ -130,6 +130,32 @@ hadamag_status hadamag_sre_mc(hadamag_ctx_t ctx, const void* psi_dev, int N, int
                               double* stderr_out, hadamag_stream_t stream);
 
 /*
+ * Thermodynamic-integration estimate of M_2, Sec. 3.2 (Eqs. Boltz to M2_TI, Algorithm 3).
+ * L Metropolis chains at beta_l = l / (L-1), l = 0..L-1, sample X-strings from
+ * Pi_beta(a) ~ exp(-beta f(a)) with f(a) = -ln(S(a) + eps), S(a) = sum_b |chi_b(a)|^4; each step
+ * proposes a one-bit flip and accepts it when u < min(1, exp(-beta (f' - f))) (FP64).  After
+ * burn_in unrecorded steps, n_s steps are averaged into the chain means <f>_l, and
+ *     I = sum_l w_l <f>_l  (composite Simpson; 3/8 rule on the last three intervals for even L),
+ *     M2_out = -log2(exp(-I) - eps)  (= I / ln 2 for eps = 0).
+ * Sign: the identity <f>_beta = -d ln Z_beta / d beta fixes I = ln Z_0 - ln Z_1; the printed
+ * return value of Algorithm 3 has the opposite sign.  Random numbers: chain l reads SplitMix64
+ * started at seed + l (as in hadamag_mc_xstrings): output 0 -> start pattern (top N bits),
+ * output 1 + 2t -> bit flipped at step t (mod N), output 2 + 2t -> u = (top 53 bits) / 2^53.
+ * Energies come from the FP32 CUDA-core per-X kernels of hadamag_sre_terms (the path setting is
+ * not used).
+ * Arguments: 1 <= N <= 24; 3 <= L <= 4096; n_s >= 1, burn_in >= 0, n_s + burn_in < 2^31;
+ * eps >= 0 (eps > 0 is needed when S(a) can vanish, e.g. stabilizer states).  means_out: L host
+ * doubles or NULL.  traj_dev: NULL or L * (burn_in + n_s) int64 on the device, 8-byte aligned,
+ * receiving traj[l * (burn_in + n_s) + t] = chain l's X-string after step t.
+ * Errors: NONFINITE when an evaluated S(a) + eps is 0 or the estimate is not finite.
+ * Synchronises `stream`.
+ */
+hadamag_status hadamag_sre_ti(hadamag_ctx_t ctx, const void* psi_dev, int N, int L, int64_t n_s,
+                              int64_t burn_in, uint64_t seed, double eps, hadamag_dtype dtype,
+                              double* M2_out, double* means_out, int64_t* traj_dev,
+                              hadamag_stream_t stream);
+
+/*
  * Mana of an N-qutrit pure state, Eq. (mana2) of Sec. 2 evaluated by the per-X-string
  * Z_3^N Fourier transform of Sec. 3.3.2 (Algorithm 5, Eqs. mana_FT and F3_unnorm_def):
  *     mana = log2( sum_{a,b} |chi_b(a)| / 3^N ),  chi = F_3^{(x)N} (alpha*_x alpha_{-x}).

@@ -24,7 +24,7 @@ EXPORTS = [
     "hadamag_launch_count", "hadamag_status_string", "hadamag_last_error", "hadamag_sre",
     "hadamag_sre_host", "hadamag_sre_terms", "hadamag_mc_xstrings", "hadamag_sre_mc",
     "hadamag_mana", "hadamag_mana_sums", "hadamag_sre_grad", "hadamag_sre_batched",
-    "hadamag_sre_noalloc", "hadamag_batched_status",
+    "hadamag_sre_noalloc", "hadamag_batched_status", "hadamag_sre_ti",
 ]
 
 
@@ -73,6 +73,7 @@ def load(path: str | None = None):
             "hadamag_sre_batched": [V, I, PV, ctypes.POINTER(I), I, PV, V, V],
             "hadamag_sre_noalloc": [V, I, D, V, V],
             "hadamag_batched_status": [V, V],
+            "hadamag_sre_ti": [V, V, I, I, L, L, U64, D, I, PD, PD, V, V],
         }
         for name, args in sig.items():
             f = getattr(lib, name)

@@ -129,6 +129,25 @@ def sre_mc(psi: torch.Tensor, samples: int, seed: int, path: int | None = None):
     return M.value, se.value
 
 
+def sre_ti(psi: torch.Tensor, L: int, n_s: int, seed: int, burn_in: int = 0, eps: float = 0.0,
+           record: bool = False):
+    """Thermodynamic-integration estimate of M_2 (Sec. 3.2, Algorithm 3): (M2_hat, chain means)
+    and, with record=True, the chains' X-strings after every step as an int64 tensor
+    [L, burn_in + n_s] on the state's device."""
+    N = _check_state(psi)
+    c = _ctx(psi)
+    M = ctypes.c_double()
+    means = (ctypes.c_double * int(L))()
+    traj = torch.empty((int(L), int(burn_in) + int(n_s)), dtype=torch.int64, device=psi.device) if record else None
+    c.check(c.lib.hadamag_sre_ti(c.h, ctypes.c_void_p(psi.data_ptr()), N, int(L), int(n_s), int(burn_in),
+                                 ctypes.c_uint64(seed & (2 ** 64 - 1)), float(eps), _dtype_code(psi),
+                                 ctypes.byref(M), means,
+                                 ctypes.c_void_p(traj.data_ptr()) if record else None, _stream(psi)),
+            "hadamag_sre_ti")
+    out = (M.value, list(means))
+    return out + (traj,) if record else out
+
+
 def mana(psi: torch.Tensor):
     """(mana in bits, sum_u |W(u)|) of an N-qutrit state (Algorithm 5, Eq. mana2)."""
     N = _check_state(psi, 3)

@@ -197,6 +197,8 @@ hadamag_status status_word(hadamag_ctx_t c) {
     int w = *c->host_status;
     if (w & ST_TIMEOUT) return fail(c, HADAMAG_ERR_TIMEOUT, "an inter-CTA wait ran out of iterations");
     if (w & ST_BADARG) return fail(c, HADAMAG_ERR_INVALID_ARG, "an X-string list entry is outside [0, dim)");
+    if (w & ST_NONPOS)
+        return fail(c, HADAMAG_ERR_NONFINITE, "S(a) + eps <= 0 at an evaluated X-string (use eps > 0)");
     return HADAMAG_OK;
 }
 

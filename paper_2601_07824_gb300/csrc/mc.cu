@@ -8,16 +8,10 @@
 // (Steele, Lea & Flood, OOPSLA 2014): output i = mix(seed + (i+1) * gamma), a_i = its top N
 // bits (samples that come out 0 are dropped), so sample i depends only on (seed, i).
 #include "extra.h"
+#include "rng.cuh"
 #include "sre_fwd.h"
 
 namespace hm {
-
-__device__ __forceinline__ uint64_t splitmix64_out(uint64_t seed, uint64_t i) {
-    uint64_t z = seed + (i + 1ull) * 0x9E3779B97F4A7C15ull;
-    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
-    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
-    return z ^ (z >> 31);
-}
 
 __global__ void mc_xstrings_kernel(uint64_t seed, int64_t count, int N, int64_t* __restrict__ out) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count;

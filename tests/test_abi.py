@@ -60,3 +60,17 @@ def test_null_context_is_rejected_without_gpu(lib):
     g = lib.hadamag_create
     g.restype = ctypes.c_int
     assert g(None, 0) == 1
+
+
+def test_typed_binding_marshals_every_argument_without_gpu():
+    # the binding's argtypes convert each Python argument; a null context returns
+    # INVALID_ARG before any CUDA call
+    import ctypes as C
+
+    from paper_2601_07824_gb300 import _lib
+    lib = _lib.load()
+    M, means = C.c_double(), (C.c_double * 4)()
+    assert lib.hadamag_sre_ti(None, None, 10, 4, 100, 10, C.c_uint64(2 ** 64 - 1), 0.0, 0, C.byref(M), means,
+                              None, None) == 1
+    assert lib.hadamag_sre_mc(None, None, 10, 100, C.c_uint64(5), 0, C.byref(M), C.byref(M), None) == 1
+    assert lib.hadamag_sre_terms(None, None, 10, 2.0, 0, None, 4, None, None) == 1
