@@ -41,7 +41,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--extra", action="store_true",
-                    help="also time N=22, mana N=11, MC N=28, batched, thermodynamic integration N=20")
+                    help="also time N=22, mana N=11, MC N=28, batched, thermodynamic integration N=20, "
+                         "mixed-state mana N=8")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--xstrings", type=int, default=0,
                     help="profiling aid: each step evaluates only the first K X-strings of the "
@@ -448,6 +449,19 @@ def extra_workloads(hm, dev, sm_count):
         return {"strings_per_s": evals * 2.0 ** 20 / dt, "evaluations_per_s": evals / dt,
                 "steps_per_s": (n_s + burn) / dt, "s": dt, "M2": r[0], "L": L, "n_s": n_s, "burn_in": burn}
     guard("ti_N20_L10", ti20)
+
+    # mixed-state mana (Algorithm 6's W) of the Sec. 3.3.3 example: the 8-qutrit marginal (sites
+    # 0..7) of a 10-qutrit brick-wall Haar state of depth 3; rho is 9^8 complex64 = 344 MB
+    # (larger than L2), read once per call
+    def mixed8():
+        psi = torch.from_numpy(inputs.brickwork_haar(10, 3, seed=1001, d=3, dtype=np.complex64)).to(dev)
+        keep = list(range(8))
+        t_rdm, rho = timed(lambda: hm.reduced_density_matrix(psi, keep), reps=3)
+        dt, r = timed(lambda: hm.mana_mixed(rho), reps=3)
+        pts = 9.0 ** 8
+        return {"points_per_s": pts / dt, "s": dt, "mana": r[0], "rho_read_GBps": pts * 8 / dt / 1e9,
+                "rdm_s": t_rdm, "rdm_tflops": 8.0 * 9.0 ** 8 * 3.0 ** 2 / t_rdm / 1e12}
+    guard("mana_mixed_N8_of_10", mixed8)
     return out
 
 

@@ -172,6 +172,35 @@ hadamag_status hadamag_mana_sums(hadamag_ctx_t ctx, const void* psi_dev, int N, 
                                  double* sums_out, hadamag_stream_t stream);
 
 /*
+ * Mana of an N-qutrit density matrix, Sec. 3.3.3 (Algorithm 6; Eq. mana with
+ * W_u = tr(rho A_u) / 3^N over the phase-space point operators A_u):
+ *     mana = log2 sum_u |W_u|  (bits; 0 for stabilizer mixtures, equal to hadamag_mana on pure states).
+ * rho_dev: 3^N x 3^N complex (dtype), row-major, rho[r * 3^N + c], qutrit j = base-3 digit j of
+ * r and c; Hermitian (W is real only then: the imaginary part is not used), trace not enforced.
+ * Computation: for every a, v_x = rho[-x - a, x - a] (digit-wise mod 3) is transformed by
+ * F_3^{(x)N} exactly as in hadamag_mana; the values are Algorithm 6's 3^N W_u up to the
+ * labelling of u, and every entry of rho is read once.
+ * sums_out (3 host doubles or NULL): [sum |chi|, sum chi, sum chi^2] over all (a, b), so that
+ * sum chi = 3^N tr rho and sum chi^2 = 3^N tr rho^2.  1 <= N <= 10 (rho is 9^N values: 28 GB of
+ * complex64 at N = 10; complex128 input is first rounded into a complex64 copy of that size).
+ * Synchronises `stream`.
+ */
+hadamag_status hadamag_mana_mixed(hadamag_ctx_t ctx, const void* rho_dev, int N, hadamag_dtype dtype,
+                                  double* mana_out, double* sums_out, hadamag_stream_t stream);
+
+/*
+ * Reduced density matrix of an N-qutrit pure state (the partial trace that gives the mixed
+ * states of Sec. 3.3.3):  rho_A[r, c] = sum_x psi[(r, x)] conj(psi[(c, x)]), where site keep[m]
+ * is base-3 digit m of r and c and x runs over the other sites.  keep: n_keep distinct sites
+ * (host ints) in [0, N); 1 <= n_keep <= min(N, 10); 1 <= N <= 16.  rho_dev: 3^n_keep x 3^n_keep
+ * complex64 on the device (row-major, 8-byte aligned), written with FP32 products summed in
+ * FP64 over chunks of 32 traced-out indices.  Stream-ordered, no synchronisation.
+ */
+hadamag_status hadamag_reduced_density_matrix(hadamag_ctx_t ctx, const void* psi_dev, int N,
+                                              hadamag_dtype dtype, const int* keep, int n_keep,
+                                              void* rho_dev, hadamag_stream_t stream);
+
+/*
  * M_2 and its Wirtinger gradient dM_2/dpsi* (not in the paper; it is what magic
  * optimisation of circuits needs).  With c_a = H^{(x)N} v_a as in Algorithm 2,
  *     dS_2/dpsi*_w = sum_a psi_{w^a} [G_a(w) + conj(G_a(w^a))],  G_a = H^{(x)N}(2|c_a|^2 c_a),

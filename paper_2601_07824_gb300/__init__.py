@@ -4,7 +4,8 @@ Implements the hot path of "Computing quantum magic of state vectors" (arXiv 260
 the exact stabilizer Renyi entropy M_n (Algorithm 2: one Walsh-Hadamard transform per
 X-string), the qutrit mana (Algorithm 5: one Z_3^N Fourier transform per X-string), a
 uniform-X Monte-Carlo M_2, the thermodynamic-integration Metropolis estimate of M_2
-(Algorithm 3), the Wirtinger gradient dM_2/dpsi*, and a batched persistent launch over many
+(Algorithm 3), the mana of qutrit density matrices (Algorithm 6) with the partial trace that
+produces them, the Wirtinger gradient dM_2/dpsi*, and a batched persistent launch over many
 states.  All arithmetic runs in hand-written sm_103a CUDA kernels in
 libhadamag.so behind a C ABI (include/hadamag.h); this package only marshals PyTorch CUDA
 tensors into that ABI.
@@ -13,7 +14,8 @@ tensors into that ABI.
 """
 from __future__ import annotations
 
-__all__ = ["sre", "sre_host", "sre_terms", "mc_xstrings", "sre_mc", "sre_ti", "mana", "mana_sums", "sre_grad",
+__all__ = ["sre", "sre_host", "sre_terms", "mc_xstrings", "sre_mc", "sre_ti", "mana", "mana_sums",
+           "mana_mixed", "reduced_density_matrix", "sre_grad",
            "SREFunction", "sre_batched", "context", "HadamagError", "PATH_AUTO",
            "PATH_CUDACORE", "PATH_TENSOR"]
 

@@ -158,6 +158,40 @@ def mana(psi: torch.Tensor):
     return m.value, sw.value
 
 
+def mana_mixed(rho: torch.Tensor):
+    """(mana in bits, [sum |chi|, sum chi, sum chi^2]) of an N-qutrit density matrix given as a
+    3^N x 3^N CUDA tensor (Algorithm 6's W via the Algorithm 5 transform, Sec. 3.3.3)."""
+    if not isinstance(rho, torch.Tensor) or not rho.is_cuda:
+        raise TypeError("rho must be a CUDA tensor")
+    if rho.dim() != 2 or rho.shape[0] != rho.shape[1] or not rho.is_contiguous():
+        raise ValueError("rho must be a contiguous square matrix")
+    n, D = 0, rho.shape[0]
+    while 3 ** n < D:
+        n += 1
+    if 3 ** n != D or n < 1:
+        raise ValueError(f"rho must be 3^N x 3^N, got {D} x {D}")
+    c = _ctx(rho)
+    m = ctypes.c_double()
+    sums = (ctypes.c_double * 3)()
+    c.check(c.lib.hadamag_mana_mixed(c.h, ctypes.c_void_p(rho.data_ptr()), n, _dtype_code(rho), ctypes.byref(m),
+                                     sums, _stream(rho)), "hadamag_mana_mixed")
+    return m.value, list(sums)
+
+
+def reduced_density_matrix(psi: torch.Tensor, keep) -> torch.Tensor:
+    """rho_A = tr_B |psi><psi| of an N-qutrit state for the sites in `keep` (site keep[m] is digit
+    m of rho_A's row and column index); complex64 [3^k, 3^k] on the state's device."""
+    N = _check_state(psi, 3)
+    keep = [int(k) for k in keep]
+    c = _ctx(psi)
+    rho = torch.empty((3 ** len(keep), 3 ** len(keep)), dtype=torch.complex64, device=psi.device)
+    arr = (ctypes.c_int * max(1, len(keep)))(*keep)
+    c.check(c.lib.hadamag_reduced_density_matrix(c.h, ctypes.c_void_p(psi.data_ptr()), N, _dtype_code(psi), arr,
+                                                 len(keep), ctypes.c_void_p(rho.data_ptr()), _stream(psi)),
+            "hadamag_reduced_density_matrix")
+    return rho
+
+
 def mana_sums(psi: torch.Tensor):
     """[sum |chi|, sum chi, sum chi^2] over all (a, b); W = chi / 3^N."""
     N = _check_state(psi, 3)

@@ -29,7 +29,7 @@ struct hadamag_ctx_s {
     hadamag_path path = HADAMAG_PATH_AUTO;
     cudaStream_t own_stream = nullptr;
     hm::DevBuf status, res, part, scratch, counters, tiles, conv, staging, alist, terms;
-    hm::DevBuf grad_acc, batch_meta, batch_sums, tc_scratch, ti_state;
+    hm::DevBuf grad_acc, batch_meta, batch_sums, tc_scratch, ti_state, rdm_idx;
     double* host_res = nullptr;
     int* host_status = nullptr;
     long long spin_limit = 1ll << 25;
@@ -41,7 +41,7 @@ struct hadamag_ctx_s {
     char last_error[256] = {0};
     std::vector<hm::DevBuf*> all_bufs() {
         return {&status, &res, &part, &scratch, &counters, &tiles, &conv, &staging, &alist, &terms,
-                &grad_acc, &batch_meta, &batch_sums, &tc_scratch, &ti_state};
+                &grad_acc, &batch_meta, &batch_sums, &tc_scratch, &ti_state, &rdm_idx};
     }
 };
 

@@ -15,6 +15,15 @@
 //   * 9 <= N <= 13: persistent two-pass kernel (same task order and bounded waits as the
 //     qubit kernel): pass 1 transforms the 8 low digits of one (a, unit) in a 3^8 tile, pass 2
 //     the N-8 high digits of 3^(N-8) units x 3^(16-N) columns and reduces.
+//
+// Mixed states (Sec. 3.3.3, Algorithm 6) run the same kernels with MIXED = true: with
+// rho = |psi><psi| the value above is rho[-x-a, x-a], and for a general density matrix
+//     v_x = rho[-x - a, x - a]   (row-major rho, qutrit j = base-3 digit j of row and column)
+// transformed the same way gives every W_u = tr(rho A_u) / 3^N (up to the labelling of u),
+// real because rho is Hermitian.  Algorithm 6 sweeps the single-qutrit 9 x 9 map over every leg
+// of the 9^N vector Vec_N(rho), N passes over it; here (a, x) -> (-x - a, x - a) is a
+// bijection onto the entries of rho, so every entry is read once and the radix-3 transform
+// stays on chip.
 #include "common.cuh"
 #include "extra.h"
 #include "mana.h"
@@ -123,20 +132,23 @@ struct PairIdx3 {
             ppos *= 3;
         }
     }
-    template <int R>
-    __device__ __forceinline__ float2 value(const float2* __restrict__ psi) const {
+    // pure: conj(psi[x - a]) psi[-x - a];  mixed: rho[-x - a, x - a] (dim = 3^N, row length)
+    template <int R, bool MIXED>
+    __device__ __forceinline__ float2 value(const float2* __restrict__ src, int64_t dim) const {
         constexpr int r0 = R % 3, r1 = (R / 3) % 3, r2 = R / 9;
         const int64_t i1 = b1 + c1[0][r0] + c1[1][r1] + c1[2][r2];
         const int64_t i2 = b2 + c2[0][r0] + c2[1][r1] + c2[2][r2];
-        return conj_mul(ld_amp(psi, i1), ld_amp(psi, i2));
+        if constexpr (MIXED) return ld_amp(src, i2 * dim + i1);
+        else return conj_mul(ld_amp(src, i1), ld_amp(src, i2));
     }
 };
 
-template <int E, int R = 0>
-__device__ __forceinline__ void load_pairs(float2 (&x)[pow3(E)], const PairIdx3& pi, const float2* __restrict__ psi) {
+template <int E, bool MIXED, int R = 0>
+__device__ __forceinline__ void load_pairs(float2 (&x)[pow3(E)], const PairIdx3& pi, const float2* __restrict__ src,
+                                           int64_t dim) {
     if constexpr (R < pow3(E)) {
-        x[R] = pi.value<R>(psi);
-        load_pairs<E, R + 1>(x, pi, psi);
+        x[R] = pi.value<R, MIXED>(src, dim);
+        load_pairs<E, MIXED, R + 1>(x, pi, src, dim);
     }
 }
 
@@ -175,7 +187,7 @@ __device__ __forceinline__ void cta_sum3(float m, float s, float q, double out[3
 
 // ---------------------------------------------------------------------------------------
 // One pass (N <= 8): a group of G = 3^(N-3) threads (1 thread for N < 3) owns one a.
-template <int N>
+template <int N, bool MIXED>
 __global__ void __launch_bounds__(256) mana_onepass(const float2* __restrict__ psi, double* __restrict__ out) {
     constexpr int E = N < 3 ? N : 3;
     constexpr int V = pow3(E);
@@ -198,7 +210,7 @@ __global__ void __launch_bounds__(256) mana_onepass(const float2* __restrict__ p
         float2 x[V];
         PairIdx3 pi;
         pi.init<E>(deposit3<E>(t, 0, S::S0), valid ? a : 0, N, S::S0);
-        load_pairs<E>(x, pi, psi);
+        load_pairs<E, MIXED>(x, pi, psi, DIM);
         reg_ft3<E, 0, E>(x);
         rounds3<N, 0, E, 1>(x, sm, t, active, SyncCta());
         float mm = 0.f, ss = 0.f, qq = 0.f;
@@ -217,7 +229,7 @@ __global__ void __launch_bounds__(256) mana_onepass(const float2* __restrict__ p
 // ---------------------------------------------------------------------------------------
 // Two passes (9 <= N <= 13).  Scratch of one a: [3^M units][3^8 columns], M = N - 8.
 // Pass-2 tile: 3^M rows x 3^(8-M) columns (3^8 values).  243 active threads of 256.
-template <int M>
+template <int M, bool MIXED>
 __global__ void __launch_bounds__(256, 2) mana_twopass(ManaParams P) {
     constexpr int D = 8, TILE = pow3(D), LOGT3 = D - M, T = pow3(LOGT3), TILES = TILE / T;
     constexpr int N = D + M;
@@ -254,7 +266,7 @@ __global__ void __launch_bounds__(256, 2) mana_twopass(ManaParams P) {
                 using S = Sched3<D, 0, 3>;
                 PairIdx3 pi;
                 pi.init<3>((int64_t)unit * TILE + deposit3<3>(t, 0, S::S0), a, N, S::S0);
-                load_pairs<3>(x, pi, P.psi);
+                load_pairs<3, MIXED>(x, pi, P.psi, PER_A);
                 reg_ft3<3, 0, 3>(x);
                 rounds3<D, 0, 3, 1>(x, smem, t, act, SyncCta());
                 if (act) {
@@ -303,13 +315,13 @@ __global__ void __launch_bounds__(256, 2) mana_twopass(ManaParams P) {
 }
 
 // ---------------------------------------------------------------------------------------
-template <int N>
+template <int N, bool MIXED>
 static cudaError_t launch_onepass_n(const float2* psi, double* out, int sm_count, int* grid, cudaStream_t st) {
     constexpr int E = N < 3 ? N : 3;
     constexpr int G = pow3(N - E);
     constexpr int GPC = 256 / G;
     const size_t smem = (size_t)GPC * pow3(N) * sizeof(float2);
-    auto k = mana_onepass<N>;
+    auto k = mana_onepass<N, MIXED>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int occ = 0;
@@ -323,9 +335,9 @@ static cudaError_t launch_onepass_n(const float2* psi, double* out, int sm_count
 
 static constexpr size_t kTwoSmem = (size_t)pow3(8) * sizeof(float2);
 
-template <int M>
+template <int M, bool MIXED>
 static cudaError_t twopass_prep(int* occ) {
-    auto k = mana_twopass<M>;
+    auto k = mana_twopass<M, MIXED>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTwoSmem);
     if (e != cudaSuccess) return e;
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, 256, kTwoSmem);
@@ -335,29 +347,31 @@ static cudaError_t twopass_prep(int* occ) {
 
 int mana_tiles_per_a(int N) { return N <= 8 ? 1 : mana::pow3(8) / mana::pow3(16 - N); }
 
-cudaError_t launch_mana_onepass(const float2* psi, int N, double* out, int sm_count, int* grid, cudaStream_t st) {
+cudaError_t launch_mana_onepass(const float2* src, int N, bool mixed, double* out, int sm_count, int* grid,
+                                cudaStream_t st) {
+#define HM_CASE(NN)                                                                              \
+    case NN:                                                                                     \
+        return mixed ? mana::launch_onepass_n<NN, true>(src, out, sm_count, grid, st)            \
+                     : mana::launch_onepass_n<NN, false>(src, out, sm_count, grid, st);
     switch (N) {
-        case 1: return mana::launch_onepass_n<1>(psi, out, sm_count, grid, st);
-        case 2: return mana::launch_onepass_n<2>(psi, out, sm_count, grid, st);
-        case 3: return mana::launch_onepass_n<3>(psi, out, sm_count, grid, st);
-        case 4: return mana::launch_onepass_n<4>(psi, out, sm_count, grid, st);
-        case 5: return mana::launch_onepass_n<5>(psi, out, sm_count, grid, st);
-        case 6: return mana::launch_onepass_n<6>(psi, out, sm_count, grid, st);
-        case 7: return mana::launch_onepass_n<7>(psi, out, sm_count, grid, st);
-        case 8: return mana::launch_onepass_n<8>(psi, out, sm_count, grid, st);
+        HM_CASE(1) HM_CASE(2) HM_CASE(3) HM_CASE(4) HM_CASE(5) HM_CASE(6) HM_CASE(7) HM_CASE(8)
         default: return cudaErrorInvalidValue;
     }
+#undef HM_CASE
 }
 
-cudaError_t mana_twopass_grid(int N, int sm_count, int* grid) {
+// Mixed states have two-pass variants for N = 9, 10 only (rho is 9^N values: 28 GB at N = 10).
+cudaError_t mana_twopass_grid(int N, bool mixed, int sm_count, int* grid) {
     int occ = 0;
     cudaError_t e;
-    switch (N) {
-        case 9: e = mana::twopass_prep<1>(&occ); break;
-        case 10: e = mana::twopass_prep<2>(&occ); break;
-        case 11: e = mana::twopass_prep<3>(&occ); break;
-        case 12: e = mana::twopass_prep<4>(&occ); break;
-        case 13: e = mana::twopass_prep<5>(&occ); break;
+    switch (N * 2 + (mixed ? 1 : 0)) {
+        case 18: e = mana::twopass_prep<1, false>(&occ); break;
+        case 20: e = mana::twopass_prep<2, false>(&occ); break;
+        case 22: e = mana::twopass_prep<3, false>(&occ); break;
+        case 24: e = mana::twopass_prep<4, false>(&occ); break;
+        case 26: e = mana::twopass_prep<5, false>(&occ); break;
+        case 19: e = mana::twopass_prep<1, true>(&occ); break;
+        case 21: e = mana::twopass_prep<2, true>(&occ); break;
         default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
@@ -365,13 +379,14 @@ cudaError_t mana_twopass_grid(int N, int sm_count, int* grid) {
     return cudaSuccess;
 }
 
-cudaError_t launch_mana_twopass(const ManaParams& P, int grid, cudaStream_t st) {
-    switch (P.N) {
-#define HM_CASE(NN)                                                                   \
-    case NN:                                                                          \
-        mana::mana_twopass<NN - 8><<<grid, 256, mana::kTwoSmem, st>>>(P);             \
+cudaError_t launch_mana_twopass(const ManaParams& P, bool mixed, int grid, cudaStream_t st) {
+    switch (P.N * 2 + (mixed ? 1 : 0)) {
+#define HM_CASE(NN, MX)                                                               \
+    case NN * 2 + MX:                                                                 \
+        mana::mana_twopass<NN - 8, MX><<<grid, 256, mana::kTwoSmem, st>>>(P);         \
         return cudaGetLastError();
-        HM_CASE(9) HM_CASE(10) HM_CASE(11) HM_CASE(12) HM_CASE(13)
+        HM_CASE(9, 0) HM_CASE(10, 0) HM_CASE(11, 0) HM_CASE(12, 0) HM_CASE(13, 0)
+        HM_CASE(9, 1) HM_CASE(10, 1)
 #undef HM_CASE
         default: return cudaErrorInvalidValue;
     }

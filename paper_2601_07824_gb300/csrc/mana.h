@@ -6,7 +6,7 @@
 namespace hm {
 
 struct ManaParams {
-    const float2* psi;
+    const float2* psi;       // the state, or the density matrix for mixed states
     int N;
     int64_t count;           // number of X-strings a (3^N)
     float2* scratch;         // R slots x A X-strings x 3^N values
@@ -22,8 +22,12 @@ struct ManaParams {
 };
 
 int mana_tiles_per_a(int N);
-cudaError_t launch_mana_onepass(const float2* psi, int N, double* out, int sm_count, int* grid, cudaStream_t st);
-cudaError_t mana_twopass_grid(int N, int sm_count, int* grid);
-cudaError_t launch_mana_twopass(const ManaParams& P, int grid, cudaStream_t st);
+// mixed = false: src is the N-qutrit state psi (3^N values, Algorithm 5); mixed = true: src is
+// a density matrix rho, 3^N x 3^N row-major (Algorithm 6's W via the same transform; the
+// two-pass variant exists for N = 9, 10).
+cudaError_t launch_mana_onepass(const float2* src, int N, bool mixed, double* out, int sm_count, int* grid,
+                                cudaStream_t st);
+cudaError_t mana_twopass_grid(int N, bool mixed, int sm_count, int* grid);
+cudaError_t launch_mana_twopass(const ManaParams& P, bool mixed, int grid, cudaStream_t st);
 
 }  // namespace hm

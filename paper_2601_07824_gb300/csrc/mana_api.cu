@@ -1,4 +1,5 @@
-// mana_api.cu -- C ABI entry points for the qutrit mana (Algorithm 5, Eq. mana2).
+// mana_api.cu -- C ABI entry points for the qutrit mana: pure states (Algorithm 5, Eq. mana2)
+// and density matrices (Algorithm 6's Wigner function, Sec. 3.3.3).
 #include <cmath>
 
 #include "ctx.h"
@@ -15,20 +16,21 @@ int64_t ipow3(int n) {
     return r;
 }
 
-// sums = [sum_{a,b} |chi_b(a)|, sum chi_b(a), sum chi_b(a)^2] (device FP64, then host).
+// sums = [sum_{a,b} |chi_b(a)|, sum chi_b(a), sum chi_b(a)^2] (device FP64, then host).  psi is
+// the state (3^N values) or, with mixed, the density matrix (3^N x 3^N, row-major).
 hadamag_status mana_sums(hadamag_ctx_t c, const void* psi, int N, hadamag_dtype dt, cudaStream_t st,
-                         double sums[3]) {
+                         double sums[3], bool mixed) {
     hadamag_status s;
     cudaError_t e;
     if ((s = begin(c, st))) return s;
     const int64_t dim = ipow3(N);
     const float2* p;
-    if ((s = as_c64(c, psi, dim, dt, st, &p))) return s;
+    if ((s = as_c64(c, psi, mixed ? dim * dim : dim, dt, st, &p))) return s;
     int64_t nparts = 0;
     if (N <= 8) {
         if ((s = ensure_buf(c, c->part, (size_t)c->sm_count * 64 * 3 * sizeof(double)))) return s;
         int grid = 0;
-        e = launch_mana_onepass(p, N, (double*)c->part.ptr, c->sm_count, &grid, st);
+        e = launch_mana_onepass(p, N, mixed, (double*)c->part.ptr, c->sm_count, &grid, st);
         c->launches++;
         if (e != cudaSuccess) return cuda_fail(c, e, "mana_onepass");
         nparts = grid;
@@ -42,7 +44,7 @@ hadamag_status mana_sums(hadamag_ctx_t c, const void* psi, int N, hadamag_dtype 
         P.n_batches = (dim + A - 1) / A;
         P.p1 = P.p2 = A * (int)ipow3(M);
         int grid = 0;
-        if ((e = mana_twopass_grid(N, c->sm_count, &grid)) != cudaSuccess) return cuda_fail(c, e, "occupancy");
+        if ((e = mana_twopass_grid(N, mixed, c->sm_count, &grid)) != cudaSuccess) return cuda_fail(c, e, "occupancy");
         const int64_t total = P.n_batches * ((int64_t)P.p1 + P.p2);
         if (grid > total) grid = (int)total;
         if ((s = ensure_buf(c, c->scratch, (size_t)P.R * A * per_a))) return s;
@@ -54,7 +56,7 @@ hadamag_status mana_sums(hadamag_ctx_t c, const void* psi, int N, hadamag_dtype 
         P.out = (double*)c->part.ptr;
         if ((e = cudaMemsetAsync(c->counters.ptr, 0, 2 * 64 * sizeof(unsigned), st)) != cudaSuccess)
             return cuda_fail(c, e, "memset counters");
-        e = launch_mana_twopass(P, grid, st);
+        e = launch_mana_twopass(P, mixed, grid, st);
         c->launches++;
         if (e != cudaSuccess) return cuda_fail(c, e, "mana_twopass");
         nparts = grid;
@@ -82,7 +84,7 @@ extern "C" hadamag_status hadamag_mana(hadamag_ctx_t c, const void* psi, int N, 
     hadamag_status s;
     if ((s = check_args(c, psi, N, dt))) return s;
     double sums[3];
-    if ((s = mana_sums(c, psi, N, dt, reinterpret_cast<cudaStream_t>(stream), sums))) return s;
+    if ((s = mana_sums(c, psi, N, dt, reinterpret_cast<cudaStream_t>(stream), sums, false))) return s;
     const double sw = sums[0] / (double)ipow3(N);  // Eq. (mana2): sum_u |W(u)| = m / 3^N
     double m = std::log2(sw);
     if (m == 0.0) m = 0.0;
@@ -98,5 +100,22 @@ extern "C" hadamag_status hadamag_mana_sums(hadamag_ctx_t c, const void* psi, in
     if (!sums_out) return fail(c, HADAMAG_ERR_INVALID_ARG, "null output");
     hadamag_status s;
     if ((s = check_args(c, psi, N, dt))) return s;
-    return mana_sums(c, psi, N, dt, reinterpret_cast<cudaStream_t>(stream), sums_out);
+    return mana_sums(c, psi, N, dt, reinterpret_cast<cudaStream_t>(stream), sums_out, false);
+}
+
+extern "C" hadamag_status hadamag_mana_mixed(hadamag_ctx_t c, const void* rho, int N, hadamag_dtype dt,
+                                             double* mana_out, double* sums_out, hadamag_stream_t stream) {
+    if (!c) return HADAMAG_ERR_INVALID_ARG;
+    if (!aligned16(rho)) return fail(c, HADAMAG_ERR_INVALID_ARG, "null or misaligned pointer");
+    if (N < 1 || N > 10) return fail(c, HADAMAG_ERR_INVALID_ARG, "mixed-state mana needs 1 <= N <= 10 (got %d)", N);
+    if (dt != HADAMAG_C64 && dt != HADAMAG_C128) return fail(c, HADAMAG_ERR_INVALID_ARG, "bad dtype");
+    double sums[3];
+    hadamag_status s;
+    if ((s = mana_sums(c, rho, N, dt, reinterpret_cast<cudaStream_t>(stream), sums, true))) return s;
+    double m = std::log2(sums[0] / (double)ipow3(N));  // sum_u |W_u|, W_u = tr(rho A_u) / 3^N
+    if (m == 0.0) m = 0.0;
+    if (mana_out) *mana_out = m;
+    if (sums_out) { sums_out[0] = sums[0]; sums_out[1] = sums[1]; sums_out[2] = sums[2]; }
+    if (!std::isfinite(m)) return fail(c, HADAMAG_ERR_NONFINITE, "non-finite mana");
+    return HADAMAG_OK;
 }
