@@ -126,6 +126,27 @@ def sre_terms(psi, q: float, a0: int = 0, a1: int | None = None, nthreads: int =
     return Sq, S1, T1
 
 
+def sre_even_sector(psi, q: float, nthreads: int = 0):
+    """(M_q, lost_norm) from the even-weight X-strings only (Sec. 3.2): for states with U(1)
+    symmetry or the Z_2 symmetry prod_j Z_j, <psi|X_a Z_b|psi> = 0 whenever |a| is odd, so the
+    2^(N-1) even-weight X-strings carry the whole sum of Eq. (sre).  Same formulas as `sre`
+    (the n -> 1 Shannon limit included) over the restricted sums."""
+    p = _c128(psi)
+    N = n_qubits(p)
+    Sq, S1, T1 = sre_terms(p, q, nthreads=nthreads)
+    a = np.arange(1 << N)
+    w = np.zeros_like(a)
+    for j in range(N):
+        w += (a >> j) & 1
+    even = (w & 1) == 0
+    sq, s1, t1 = float(Sq[even].sum()), float(S1[even].sum()), float(T1[even].sum())
+    if q == 1.0:
+        M = -t1 / s1 + np.log2(s1) - N
+    else:
+        M = np.log2(sq / 2.0 ** N) / (1.0 - q)
+    return float(M), 1.0 - s1 / 2.0 ** N
+
+
 def sre_terms_list(psi, a_list, nthreads: int = 0) -> np.ndarray:
     """S(a) = sum_b |chi_b(a)|^4 for an explicit list of X-strings."""
     lib, p = _load(), _c128(psi)

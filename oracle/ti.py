@@ -21,6 +21,12 @@ Readings (the printed text is inconsistent here):
     symmetric proposal: one uniformly chosen bit of a) and one output, as a double in [0, 1)
     from its top 53 bits, decides acceptance; the start pattern is the top N bits of the
     chain's first output.
+  * Even sector (sector="even", Sec. 3.2's restriction of the chain for U(1) or Z_2^Z symmetric
+    states, whose odd-weight X-strings have S(a) = 0): the chains stay on even-weight a.  The
+    start pattern gets its bit 0 flipped when its weight is odd; each step flips two distinct
+    bits drawn from the step's first output r as b1 = r mod N, b2 = (r div N) mod (N-1),
+    b2 += 1 if b2 >= b1 (a symmetric move that spans the sector).  Then Z_0 = 2^(N-1),
+    Z_1 = S_2 + 2^(N-1) eps and M_2 = 1 - log2(exp(-I) - eps).
 """
 from __future__ import annotations
 
@@ -57,8 +63,18 @@ def energy_fn(psi, eps: float = 0.0):
     return f
 
 
+def even_mask(N: int) -> np.ndarray:
+    """True at the even-weight X-strings a in [0, 2^N)."""
+    a = np.arange(1 << N)
+    w = np.zeros_like(a)
+    for j in range(N):
+        w += (a >> j) & 1
+    return (w & 1) == 0
+
+
 def boltzmann_mean(f: np.ndarray, beta: float) -> float:
-    """<f>_beta = sum_a Pi_beta(a) f(a), Eq. f_expect_beta_reg, by enumeration over all a."""
+    """<f>_beta = sum_a Pi_beta(a) f(a), Eq. f_expect_beta_reg, by enumeration over the given
+    energies (all a, or the sector's)."""
     x = -beta * f
     w = np.exp(x - x.max())
     return float(np.sum(w * f) / np.sum(w))
@@ -85,20 +101,47 @@ def simpson_weights(L: int) -> np.ndarray:
     return w
 
 
-def m2_from_integral(I: float, eps: float = 0.0) -> float:
-    """M_2 = -log2(exp(-I) - eps) (Eq. M2_TI_reg_explicit_correct with the sign reading)."""
-    return -math.log2(math.exp(-I) - eps)
+def m2_from_integral(I: float, eps: float = 0.0, sector: str | None = None) -> float:
+    """M_2 = -log2(exp(-I) - eps) (Eq. M2_TI_reg_explicit_correct with the sign reading); in
+    the even sector Z_0 = 2^(N-1), so M_2 = 1 - log2(exp(-I) - eps)."""
+    return -math.log2(math.exp(-I) - eps) + (1.0 if sector == "even" else 0.0)
 
 
-def m2_ti_exact(psi, L: int, eps: float = 0.0) -> float:
+def m2_ti_exact(psi, L: int, eps: float = 0.0, sector: str | None = None) -> float:
     """Thermodynamic integration with the exact integrand <f>_beta (quadrature error only)."""
-    f = energies(psi, eps)
+    f = energies(psi, eps) if sector is None else energies_sector(psi, eps, sector)
     betas = np.linspace(0.0, 1.0, L)
     I = float(np.dot(simpson_weights(L), [boltzmann_mean(f, b) for b in betas]))
-    return m2_from_integral(I, eps)
+    return m2_from_integral(I, eps, sector)
 
 
-def metropolis_means(f, N: int, L: int, n_s: int, seed: int, burn_in: int = 0, record: dict | None = None):
+def energy_table(psi, eps: float = 0.0, sector: str | None = None) -> np.ndarray:
+    """f[a] for every a; with sector="even" only the even-weight entries are evaluated (and must
+    be finite), the others are +inf, which a chain kept in the sector never reads."""
+    if sector is None:
+        return energies(psi, eps)
+    fs = energies_sector(psi, eps, sector)
+    N = int(round(math.log2(np.asarray(psi).size)))
+    f = np.full(1 << N, np.inf)
+    f[even_mask(N)] = fs
+    return f
+
+
+def energies_sector(psi, eps: float, sector: str) -> np.ndarray:
+    """Energies of the sector's X-strings only (sector = "even")."""
+    import oracle
+    if sector != "even":
+        raise ValueError("sector must be 'even'")
+    Sq, _, _ = oracle.sre_terms(psi, 2.0)
+    N = int(round(math.log2(Sq.size)))
+    S = Sq[even_mask(N)] + eps
+    if np.any(S <= 0.0):
+        raise ValueError("S(a) + eps must be positive for every a of the sector (use eps > 0)")
+    return -np.log(S)
+
+
+def metropolis_means(f, N: int, L: int, n_s: int, seed: int, burn_in: int = 0, record: dict | None = None,
+                     sector: str | None = None):
     """Algorithm 3's chains: per beta_l, n_s Metropolis steps (one-bit flips, acceptance
     min(1, exp(-beta (f' - f)))) after `burn_in` unrecorded ones; returns (means, visits)
     with visits[l][a] = how often the recorded chain state was a.
@@ -106,7 +149,7 @@ def metropolis_means(f, N: int, L: int, n_s: int, seed: int, burn_in: int = 0, r
     f is the energy table (f[a] for every a) or a callable a -> f(a).  With `record` given,
     record["traj"][l, t] is the chain state after step t (burn-in included) and
     record["margin"][l, t] = |u - p_acc| of that step's decision (how far the decision was
-    from going the other way)."""
+    from going the other way).  sector="even" keeps the chains on even-weight X-strings."""
     import oracle
     energy = f if callable(f) else f.__getitem__
     betas = np.linspace(0.0, 1.0, L)
@@ -119,12 +162,20 @@ def metropolis_means(f, N: int, L: int, n_s: int, seed: int, burn_in: int = 0, r
     for l, beta in enumerate(betas):
         r = oracle.splitmix64(seed + l, 1 + 2 * steps)
         a = int(r[0] >> np.uint64(64 - N)) if N > 0 else 0
+        if sector == "even" and bin(a).count("1") % 2 == 1:
+            a ^= 1
         fa = energy(a)
         acc = 0.0
         for t in range(steps):
-            bit = int(r[1 + 2 * t] % np.uint64(N))
             u = float(r[2 + 2 * t] >> np.uint64(11)) * 2.0 ** -53
-            a2 = a ^ (1 << bit)
+            if sector == "even":
+                b1 = int(r[1 + 2 * t] % np.uint64(N))
+                b2 = int((r[1 + 2 * t] // np.uint64(N)) % np.uint64(N - 1))
+                if b2 >= b1:
+                    b2 += 1
+                a2 = a ^ (1 << b1) ^ (1 << b2)
+            else:
+                a2 = a ^ (1 << int(r[1 + 2 * t] % np.uint64(N)))
             f2 = energy(a2)
             p_acc = math.exp(min(0.0, -beta * (f2 - fa)))
             if u < p_acc:
@@ -141,11 +192,11 @@ def metropolis_means(f, N: int, L: int, n_s: int, seed: int, burn_in: int = 0, r
 
 
 def m2_metropolis(psi, L: int, n_s: int, seed: int, burn_in: int = 0, eps: float = 0.0,
-                  record: dict | None = None) -> float:
+                  record: dict | None = None, sector: str | None = None) -> float:
     """Algorithm 3 (with the sign reading): M_2 estimate from L chains of n_s samples.  Up to
     12 qubits the energy table is built for every a; beyond, energies are evaluated on demand."""
     psi = np.asarray(psi)
     N = int(round(math.log2(psi.size)))
-    f = energies(psi, eps) if N <= 12 else energy_fn(psi, eps)
-    means, _ = metropolis_means(f, N, L, n_s, seed, burn_in, record)
-    return m2_from_integral(float(np.dot(simpson_weights(L), means)), eps)
+    f = energy_table(psi, eps, sector) if N <= 12 else energy_fn(psi, eps)
+    means, _ = metropolis_means(f, N, L, n_s, seed, burn_in, record, sector)
+    return m2_from_integral(float(np.dot(simpson_weights(L), means)), eps, sector)

@@ -46,6 +46,45 @@ def gaussian_state(N: int, seed: int, d: int = 2, dtype=np.complex128) -> np.nda
     return g.astype(dtype)
 
 
+def _popcount(z: np.ndarray) -> np.ndarray:
+    z = z.astype(np.int64)
+    c = np.zeros_like(z)
+    while np.any(z):
+        c += z & 1
+        z >>= 1
+    return c
+
+
+def u1_state(N: int, k: int, seed: int, dtype=np.complex128) -> np.ndarray:
+    """U(1)-symmetric qubit state: i.i.d. complex Gaussian amplitudes on the basis states of
+    Hamming weight k (fixed total magnetisation), zero elsewhere, normalised.
+
+    Draw order: real parts, then imaginary parts of the supported amplitudes in index order."""
+    z = np.arange(2 ** N)
+    sup = np.nonzero(_popcount(z) == k)[0]
+    rng = np.random.default_rng(seed)
+    re = rng.standard_normal(sup.size)
+    im = rng.standard_normal(sup.size)
+    v = np.zeros(2 ** N, dtype=np.complex128)
+    v[sup] = re + 1j * im
+    v /= np.linalg.norm(v)
+    return v.astype(dtype)
+
+
+def parity_state(N: int, seed: int, parity: int = 0, dtype=np.complex128) -> np.ndarray:
+    """Z_2-symmetric qubit state (eigenstate of prod_j Z_j): i.i.d. complex Gaussian amplitudes
+    on the basis states of the given Hamming-weight parity, zero elsewhere, normalised."""
+    z = np.arange(2 ** N)
+    sup = np.nonzero((_popcount(z) & 1) == parity)[0]
+    rng = np.random.default_rng(seed)
+    re = rng.standard_normal(sup.size)
+    im = rng.standard_normal(sup.size)
+    v = np.zeros(2 ** N, dtype=np.complex128)
+    v[sup] = re + 1j * im
+    v /= np.linalg.norm(v)
+    return v.astype(dtype)
+
+
 def zero_state(N: int, d: int = 2, dtype=np.complex128) -> np.ndarray:
     v = np.zeros(_dim(N, d), dtype=dtype)
     v[0] = 1.0

@@ -137,3 +137,89 @@ def test_recorded_trajectory_is_a_valid_chain():
         np.testing.assert_array_equal(np.bincount(traj[l, burn:], minlength=1 << N), visits[l])
     # beta = 0 accepts every proposal
     assert np.all(traj[0] != np.concatenate(([int(oracle.splitmix64(11, 1)[0] >> np.uint64(64 - N))], traj[0, :-1])))
+
+
+# ---- even sector (Sec. 3.2: U(1) / Z_2^Z symmetric states, odd-weight X-sectors vanish) ----
+
+def symmetric_states():
+    # U(1) states at half filling (k = N/2 or (N-1)/2): X_a can map weight-k states onto
+    # weight-k states only if |a|/2 <= min(k, N-k), so away from half filling some even-weight
+    # sectors vanish as well (see the next test)
+    return [("u1", I.u1_state(8, 4, 21)), ("u1_odd_N", I.u1_state(7, 3, 22)), ("z2_even", I.parity_state(8, 23)),
+            ("z2_odd", I.parity_state(7, 24, parity=1))]
+
+
+def test_u1_away_from_half_filling_keeps_vanishing_even_sectors():
+    N, k = 8, 3
+    Sq, _, _ = oracle.sre_terms(I.u1_state(N, k, 21), 2.0)
+    a = np.arange(1 << N)
+    wt = np.array([bin(x).count("1") for x in a])
+    assert np.abs(Sq[wt > 2 * min(k, N - k)]).max() < 1e-14  # |a| = 8 > 6: S(a) = 0
+    assert Sq[(wt % 2 == 0) & (wt <= 2 * min(k, N - k))].min() > 0.0
+    with pytest.raises(ValueError):  # the even-sector chain then needs eps > 0 too
+        ti.energies_sector(I.u1_state(N, k, 21), 0.0, "even")
+    assert ti.m2_ti_exact(I.u1_state(N, k, 21), 65, eps=1e-9, sector="even") == pytest.approx(
+        oracle.sre(I.u1_state(N, k, 21), 2.0)[0], abs=1e-4)
+
+
+@pytest.mark.parametrize("label,psi", symmetric_states())
+def test_odd_sectors_vanish_and_even_sector_sre_is_exact(label, psi):
+    N = int(round(math.log2(psi.size)))
+    Sq, S1, _ = oracle.sre_terms(psi, 2.0)
+    odd = ~ti.even_mask(N)
+    assert np.abs(Sq[odd]).max() < 1e-14 and np.abs(S1[odd]).max() < 1e-14
+    for q in (1.0, 2.0, 3.0):
+        M, lost = oracle.sre(psi, q)
+        Me, loste = oracle.sre_even_sector(psi, q)
+        assert Me == pytest.approx(M, abs=1e-11), q
+        assert loste == pytest.approx(lost, abs=1e-12)
+
+
+def test_even_sector_sre_differs_on_a_generic_state():
+    psi = I.gaussian_state(7, 25)
+    assert abs(oracle.sre_even_sector(psi, 2.0)[0] - oracle.sre(psi, 2.0)[0]) > 0.1
+
+
+@pytest.mark.parametrize("label,psi", symmetric_states())
+def test_even_sector_integral_converges_to_exact_m2(label, psi):
+    M2 = oracle.sre(psi, 2.0)[0]
+    e17 = abs(ti.m2_ti_exact(psi, 17, sector="even") - M2)
+    e33 = abs(ti.m2_ti_exact(psi, 33, sector="even") - M2)
+    assert e33 < 2e-6 * max(1.0, M2) and e33 < e17 / 6
+    # without the sector the odd X-strings have S = 0: only eps > 0 makes the full chain valid,
+    # and then both agree with M_2 up to the eps bias
+    with pytest.raises(ValueError):
+        ti.energies(psi)
+
+
+def test_even_sector_chains_stay_in_the_sector_and_sample_it():
+    psi = I.u1_state(7, 3, 26)
+    N = 7
+    f = ti.energy_table(psi, 0.0, "even")
+    rec = {}
+    means, visits = ti.metropolis_means(f, N, 3, 100000, seed=31, burn_in=1000, record=rec, sector="even")
+    w = np.array([[bin(int(a)).count("1") % 2 for a in row] for row in rec["traj"]])
+    assert not w.any()
+    even = ti.even_mask(N)
+    for l, beta in enumerate((0.0, 0.5, 1.0)):
+        p = np.where(even, np.exp(-beta * np.where(even, f, 0.0)), 0.0)
+        p /= p.sum()
+        emp = visits[l] / visits[l].sum()
+        assert 0.5 * np.abs(emp - p).sum() < 0.04, beta
+    M2 = oracle.sre(psi, 2.0)[0]
+    assert ti.m2_metropolis(psi, 9, 20000, 5, burn_in=500, sector="even") == pytest.approx(M2, rel=0.02)
+
+
+def test_even_sector_planted_mistakes_fail():
+    psi = I.parity_state(7, 27)
+    M2 = oracle.sre(psi, 2.0)[0]
+    f = ti.energies_sector(psi, 0.0, "even")
+    betas = np.linspace(0.0, 1.0, 33)
+    I_ = float(np.dot(ti.simpson_weights(33), [ti.boltzmann_mean(f, b) for b in betas]))
+    # dropping the log2(2^N / Z_0) = 1 shift is off by one bit
+    assert abs(ti.m2_from_integral(I_) - M2) == pytest.approx(1.0, abs=1e-5)
+    assert ti.m2_from_integral(I_, sector="even") == pytest.approx(M2, abs=1e-5)
+    # one-bit proposals leave the sector at the first step
+    rec = {}
+    ti.metropolis_means(ti.energies(psi, 1e-3), 7, 3, 50, seed=3, record=rec)
+    assert any(bin(int(a)).count("1") % 2 for a in rec["traj"].ravel())
