@@ -87,6 +87,17 @@ hadamag_status hadamag_sre(hadamag_ctx_t ctx, const void* psi_dev, int N, double
                            hadamag_dtype dtype, double* M_out, double* lost_norm_out,
                            hadamag_stream_t stream);
 
+/*
+ * hadamag_sre over the even-weight X-strings only (Sec. 3.2): for states with U(1) symmetry
+ * (conserved sum_j Z_j) or the Z_2 symmetry prod_j Z_j, <psi|X_a Z_b|psi> = 0 whenever |a| is
+ * odd, so the 2^(N-1) even-weight X-strings a = 2i + parity(i) carry all of Eq. (sre) and the
+ * work halves.  Same outputs, limits and path selection as hadamag_sre; the symmetry is the
+ * caller's claim (for other states the result is the even-sector part only).
+ */
+hadamag_status hadamag_sre_even_sector(hadamag_ctx_t ctx, const void* psi_dev, int N, double n,
+                                       hadamag_dtype dtype, double* M_out, double* lost_norm_out,
+                                       hadamag_stream_t stream);
+
 /* Same as hadamag_sre with psi in HOST memory: the call copies it to the device on the
  * context's own stream (inside the call), computes, and returns host results. */
 hadamag_status hadamag_sre_host(hadamag_ctx_t ctx, const void* psi_host, int N, double n,
@@ -141,6 +152,12 @@ hadamag_status hadamag_sre_mc(hadamag_ctx_t ctx, const void* psi_dev, int N, int
  * return value of Algorithm 3 has the opposite sign.  Random numbers: chain l reads SplitMix64
  * started at seed + l (as in hadamag_mc_xstrings): output 0 -> start pattern (top N bits),
  * output 1 + 2t -> bit flipped at step t (mod N), output 2 + 2t -> u = (top 53 bits) / 2^53.
+ * sector = 1 restricts the chains to even-weight X-strings, the sectors that survive a U(1) or
+ * prod_j Z_j symmetry (Sec. 3.2; N >= 2): the start pattern has bit 0 flipped when its weight
+ * is odd, a move flips bits b1 = r mod N and b2 = (r div N) mod (N-1) (+1 if b2 >= b1) of step
+ * output r, and Z_0 = 2^(N-1) gives M2_out = 1 - log2(exp(-I) - eps).  Valid only for states
+ * whose odd-weight sectors vanish; sectors that also vanish (U(1) away from half filling)
+ * still need eps > 0.
  * Energies come from the FP32 CUDA-core per-X kernels of hadamag_sre_terms (the path setting is
  * not used).
  * Arguments: 1 <= N <= 24; 3 <= L <= 4096; n_s >= 1, burn_in >= 0, n_s + burn_in < 2^31;
@@ -151,9 +168,9 @@ hadamag_status hadamag_sre_mc(hadamag_ctx_t ctx, const void* psi_dev, int N, int
  * Synchronises `stream`.
  */
 hadamag_status hadamag_sre_ti(hadamag_ctx_t ctx, const void* psi_dev, int N, int L, int64_t n_s,
-                              int64_t burn_in, uint64_t seed, double eps, hadamag_dtype dtype,
-                              double* M2_out, double* means_out, int64_t* traj_dev,
-                              hadamag_stream_t stream);
+                              int64_t burn_in, uint64_t seed, double eps, int sector,
+                              hadamag_dtype dtype, double* M2_out, double* means_out,
+                              int64_t* traj_dev, hadamag_stream_t stream);
 
 /*
  * Mana of an N-qutrit pure state, Eq. (mana2) of Sec. 2 evaluated by the per-X-string

@@ -328,6 +328,38 @@ hadamag_status sre_from_sums(hadamag_ctx_t c, int N, double n, const double sums
 
 }  // namespace hm
 
+extern "C" hadamag_status hadamag_sre_even_sector(hadamag_ctx_t c, const void* psi, int N, double n,
+                                                  hadamag_dtype dt, double* M_out, double* lost_out,
+                                                  hadamag_stream_t stream) {
+    if (!c) return HADAMAG_ERR_INVALID_ARG;
+    if (!aligned16(psi) || !M_out) return fail(c, HADAMAG_ERR_INVALID_ARG, "null or misaligned pointer");
+    if (N < 1 || N > 24) return fail(c, HADAMAG_ERR_INVALID_ARG, "N must be in [1, 24] (got %d)", N);
+    if (!(n > 0.0) || !std::isfinite(n)) return fail(c, HADAMAG_ERR_INVALID_ARG, "n must be > 0");
+    if (dt != HADAMAG_C64 && dt != HADAMAG_C128) return fail(c, HADAMAG_ERR_INVALID_ARG, "bad dtype");
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    hadamag_status s;
+    cudaError_t e;
+    if ((s = begin(c, st))) return s;
+    const float2* p;
+    if ((s = as_c64(c, psi, int64_t(1) << N, dt, st, &p))) return s;
+    const int64_t count = int64_t(1) << (N - 1);
+    if ((s = ensure_buf(c, c->alist, (size_t)count * sizeof(int64_t)))) return s;
+    int64_t* al = (int64_t*)c->alist.ptr;
+    e = launch_even_xstrings(count, al, st);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(c, e, "even_xstrings");
+    int64_t nparts = 0;
+    if (use_tensor_path(c, N, n)) s = run_sre_tensor(c, p, N, n, count, al, 0, nullptr, st, &nparts);
+    else s = run_sre(c, p, N, n, count, al, 0, nullptr, st, &nparts);
+    if (s) return s;
+    e = launch_sum_triples((const double*)c->part.ptr, nparts, (double*)c->res.ptr, st);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(c, e, "sum_triples");
+    if ((s = finish(c, (const double*)c->res.ptr, 3, st))) return s;
+    const double sums[3] = {c->host_res[0], c->host_res[1], c->host_res[2]};
+    return sre_from_sums(c, N, n, sums, M_out, lost_out);
+}
+
 extern "C" hadamag_status hadamag_sre_host(hadamag_ctx_t c, const void* psi_host, int N, double n,
                                            hadamag_dtype dt, double* M_out, double* lost_out) {
     if (!c) return HADAMAG_ERR_INVALID_ARG;

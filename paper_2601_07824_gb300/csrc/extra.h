@@ -10,6 +10,7 @@ namespace hm {
 // Monte-Carlo helpers (mc.cu)
 cudaError_t launch_mc_xstrings(uint64_t seed, int64_t count, int N, int64_t* out, cudaStream_t st);
 cudaError_t launch_mc_stats(const double* terms, const int64_t* a_list, int64_t count, double* out4, cudaStream_t st);
+cudaError_t launch_even_xstrings(int64_t count, int64_t* out, cudaStream_t st);
 hadamag_status run_sre_hbm_terms(hadamag_ctx_t c, const float2* psi, int N, int64_t count,
                                  const int64_t* a_list, double* terms, cudaStream_t st);
 

@@ -54,6 +54,20 @@ __global__ void mc_stats_kernel(const double* __restrict__ t, const int64_t* __r
     }
 }
 
+// The 2^(N-1) even-weight X-strings: a_i = 2i + parity(i), a bijection from [0, 2^(N-1)) onto
+// the even-weight a in [0, 2^N) (the X-sectors that survive a U(1) or prod_j Z_j symmetry).
+__global__ void even_xstrings_kernel(int64_t count, int64_t* __restrict__ out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < count; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] = (i << 1) | (int64_t)(__popcll((unsigned long long)i) & 1);
+}
+
+cudaError_t launch_even_xstrings(int64_t count, int64_t* out, cudaStream_t st) {
+    int64_t blocks = (count + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    even_xstrings_kernel<<<(unsigned)blocks, 256, 0, st>>>(count, out);
+    return cudaGetLastError();
+}
+
 cudaError_t launch_mc_xstrings(uint64_t seed, int64_t count, int N, int64_t* out, cudaStream_t st) {
     int64_t blocks = (count + 255) / 256;
     if (blocks > 4096) blocks = 4096;

@@ -12,10 +12,9 @@
 // The chains are independent, so one step of all L chains is one batch of L per-X-string
 // evaluations: the per-X kernels of Algorithm 2 (run_sre with per_a = 1, CUDA-core path) on the
 // L proposals, then ti_step, one thread per chain, which decides, records and proposes the next
-// move.  Random numbers are counter-based: chain l reads the SplitMix64 stream started at
-// seed + l; output 0 gives the start pattern (its top N bits), output 1 + 2t the bit flipped at
-// step t (mod N, a symmetric one-bit proposal) and output 2 + 2t the acceptance variate
-// u = (top 53 bits) / 2^53.  The decision u < exp(min(0, -beta (f' - f))) is taken in FP64.
+// move.  Random numbers are counter-based (the draws and moves are defined in ti.cuh); with
+// sector = 1 the chains stay on even-weight X-strings (two-bit moves) and Z_0 = 2^(N-1).  The
+// decision u < exp(min(0, -beta (f' - f))) is taken in FP64.
 #include <cmath>
 #include <vector>
 
@@ -37,6 +36,7 @@ struct TiChains {
     double eps;
     int64_t T, burn_in, n_s;
     int L, N;
+    int even;  // 1: chains restricted to even-weight X-strings
 };
 
 __device__ __forceinline__ double ti_energy(const TiChains& c, double S) {
@@ -49,7 +49,7 @@ __device__ __forceinline__ double ti_energy(const TiChains& c, double S) {
 __global__ void ti_start(TiChains c) {
     const int l = blockIdx.x * blockDim.x + threadIdx.x;
     if (l >= c.L) return;
-    const int64_t a = ti_start_pattern(c.seed, l, c.N);
+    const int64_t a = ti_start_pattern(c.seed, l, c.N, c.even);
     c.a[l] = a;
     c.prop[l] = a;
 }
@@ -60,7 +60,7 @@ __global__ void ti_init(TiChains c) {
     if (l >= c.L) return;
     c.f[l] = ti_energy(c, c.terms[3 * l]);
     c.acc[l] = 0.0;
-    c.prop[l] = c.a[l] ^ (int64_t(1) << ti_flip_bit(c.seed, l, 0, c.N));
+    c.prop[l] = c.a[l] ^ ti_move(c.seed, l, 0, c.N, c.even);
 }
 
 // step t: accept or reject the evaluated proposal, record, propose step t + 1
@@ -78,7 +78,7 @@ __global__ void ti_step(TiChains c, int64_t t) {
     }
     if (t >= c.burn_in) c.acc[l] += fa;
     if (c.traj) c.traj[(int64_t)l * c.T + t] = a;
-    if (t + 1 < c.T) c.prop[l] = a ^ (int64_t(1) << ti_flip_bit(c.seed, l, t + 1, c.N));
+    if (t + 1 < c.T) c.prop[l] = a ^ ti_move(c.seed, l, t + 1, c.N, c.even);
 }
 
 // chain means, the quadrature I (fixed order) and M_2
@@ -91,7 +91,7 @@ __global__ void ti_finish(TiChains c) {
         I += ti_simpson_weight(l, c.L) * m;
     }
     c.out[c.L] = I;
-    c.out[c.L + 1] = ti_m2(I, c.eps);
+    c.out[c.L + 1] = ti_m2(I, c.eps, c.even);
 }
 
 }  // namespace hm
@@ -99,9 +99,9 @@ __global__ void ti_finish(TiChains c) {
 using namespace hm;
 
 extern "C" hadamag_status hadamag_sre_ti(hadamag_ctx_t c, const void* psi, int N, int L, int64_t n_s,
-                                         int64_t burn_in, uint64_t seed, double eps, hadamag_dtype dt,
-                                         double* M2_out, double* means_out, int64_t* traj_dev,
-                                         hadamag_stream_t stream) {
+                                         int64_t burn_in, uint64_t seed, double eps, int sector,
+                                         hadamag_dtype dt, double* M2_out, double* means_out,
+                                         int64_t* traj_dev, hadamag_stream_t stream) {
     if (!c) return HADAMAG_ERR_INVALID_ARG;
     if (!aligned16(psi) || !M2_out) return fail(c, HADAMAG_ERR_INVALID_ARG, "null or misaligned pointer");
     if (traj_dev && (reinterpret_cast<uintptr_t>(traj_dev) & 7))
@@ -111,6 +111,8 @@ extern "C" hadamag_status hadamag_sre_ti(hadamag_ctx_t c, const void* psi, int N
     if (n_s < 1 || burn_in < 0 || n_s > (int64_t(1) << 31) - 1 - burn_in)
         return fail(c, HADAMAG_ERR_INVALID_ARG, "need n_s >= 1, burn_in >= 0, n_s + burn_in < 2^31");
     if (!(eps >= 0.0) || !std::isfinite(eps)) return fail(c, HADAMAG_ERR_INVALID_ARG, "eps must be finite and >= 0");
+    if (sector != 0 && sector != 1) return fail(c, HADAMAG_ERR_INVALID_ARG, "sector must be 0 (all) or 1 (even)");
+    if (sector == 1 && N < 2) return fail(c, HADAMAG_ERR_INVALID_ARG, "the even sector needs N >= 2");
     if (dt != HADAMAG_C64 && dt != HADAMAG_C128) return fail(c, HADAMAG_ERR_INVALID_ARG, "bad dtype");
     cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
     hadamag_status s;
@@ -137,6 +139,7 @@ extern "C" hadamag_status hadamag_sre_ti(hadamag_ctx_t c, const void* psi, int N
     ch.n_s = n_s;
     ch.L = L;
     ch.N = N;
+    ch.even = sector;
     double* terms = (double*)c->terms.ptr;
     const unsigned grid = (unsigned)((L + 127) / 128);
     ti_start<<<grid, 128, 0, st>>>(ch);

@@ -2,8 +2,12 @@
 // Algorithm 3), host- and device-callable so that the same code drives the kernels in ti.cu.
 //
 // Chain l reads the SplitMix64 stream started at seed + l: output 0 gives the start pattern
-// (its top N bits), output 1 + 2t the bit flipped at step t (mod N, a symmetric one-bit
-// proposal) and output 2 + 2t the acceptance variate u = (top 53 bits) / 2^53 in [0, 1).
+// (its top N bits), output 1 + 2t the move of step t and output 2 + 2t the acceptance variate
+// u = (top 53 bits) / 2^53 in [0, 1).  A move flips one bit (r mod N) or, in the even sector,
+// two distinct bits b1 = r mod N, b2 = (r div N) mod (N-1) (+1 when b2 >= b1): a symmetric
+// proposal that keeps the Hamming-weight parity (Sec. 3.2: for U(1) or prod_j Z_j symmetric
+// states the odd-weight X-sectors have S(a) = 0); the even-sector start pattern has its bit 0
+// flipped when its weight is odd.
 #pragma once
 #include <math.h>
 #include <stdint.h>
@@ -17,12 +21,25 @@ __host__ __device__ __forceinline__ double ti_beta(int l, int L) {
     return l == L - 1 ? 1.0 : (double)l * (1.0 / (double)(L - 1));
 }
 
-__host__ __device__ __forceinline__ int64_t ti_start_pattern(uint64_t seed, int l, int N) {
-    return (int64_t)(splitmix64_out(seed + (uint64_t)l, 0) >> (64 - N));
+__host__ __device__ __forceinline__ int ti_parity(int64_t a) {
+    uint64_t v = (uint64_t)a;
+    v ^= v >> 32; v ^= v >> 16; v ^= v >> 8; v ^= v >> 4; v ^= v >> 2; v ^= v >> 1;
+    return (int)(v & 1);
 }
 
-__host__ __device__ __forceinline__ int ti_flip_bit(uint64_t seed, int l, int64_t t, int N) {
-    return (int)(splitmix64_out(seed + (uint64_t)l, (uint64_t)(1 + 2 * t)) % (uint64_t)N);
+__host__ __device__ __forceinline__ int64_t ti_start_pattern(uint64_t seed, int l, int N, int even) {
+    const int64_t a = (int64_t)(splitmix64_out(seed + (uint64_t)l, 0) >> (64 - N));
+    return (even && ti_parity(a)) ? (a ^ 1) : a;
+}
+
+// XOR mask of the move proposed at step t
+__host__ __device__ __forceinline__ int64_t ti_move(uint64_t seed, int l, int64_t t, int N, int even) {
+    const uint64_t r = splitmix64_out(seed + (uint64_t)l, (uint64_t)(1 + 2 * t));
+    const int b1 = (int)(r % (uint64_t)N);
+    if (!even) return int64_t(1) << b1;
+    int b2 = (int)((r / (uint64_t)N) % (uint64_t)(N - 1));
+    if (b2 >= b1) ++b2;
+    return (int64_t(1) << b1) | (int64_t(1) << b2);
 }
 
 __host__ __device__ __forceinline__ double ti_uniform(uint64_t seed, int l, int64_t t) {
@@ -48,7 +65,10 @@ __host__ __device__ __forceinline__ double ti_simpson_weight(int l, int L) {
     return w;
 }
 
-// M_2 from the quadrature I of the chain means: I = ln Z_0 - ln Z_1 = -ln((S_2 + 2^N eps) / 2^N)
-__host__ __device__ __forceinline__ double ti_m2(double I, double eps) { return -log2(exp(-I) - eps); }
+// M_2 from the quadrature I of the chain means, I = ln Z_0 - ln Z_1 with Z_1 = S_2 + Z_0 eps:
+// Z_0 = 2^N gives -log2(exp(-I) - eps); the even sector (Z_0 = 2^(N-1)) adds 1
+__host__ __device__ __forceinline__ double ti_m2(double I, double eps, int even) {
+    return -log2(exp(-I) - eps) + (even ? 1.0 : 0.0);
+}
 
 }  // namespace hm

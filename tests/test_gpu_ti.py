@@ -36,15 +36,25 @@ TOL_F = 2e-5
 TOL_M = 3e-5
 
 
-def check_against_oracle(psi_np, L, n_s, burn, seed, eps=0.0):
+def move_mask(r, N, sector):
+    """The generator's move for output r (the oracle's rule, restated for the validity check)."""
+    b1 = int(r % np.uint64(N))
+    if sector != "even":
+        return 1 << b1
+    b2 = int((r // np.uint64(N)) % np.uint64(N - 1))
+    return (1 << b1) | (1 << (b2 + (b2 >= b1)))
+
+
+def check_against_oracle(psi_np, L, n_s, burn, seed, eps=0.0, sector=None):
     N = int(psi_np.size).bit_length() - 1
     psi = torch.from_numpy(psi_np).to(DEV)
-    M2, means, traj = hm.sre_ti(psi, L, n_s, seed, burn_in=burn, eps=eps, record=True)
+    M2, means, traj = hm.sre_ti(psi, L, n_s, seed, burn_in=burn, eps=eps, record=True,
+                                even_sector=sector == "even")
     traj = traj.cpu().numpy()
     rec = {}
-    f = ti.energies(psi_np, eps) if N <= 12 else ti.energy_fn(psi_np, eps)
-    means_o, _ = ti.metropolis_means(f, N, L, n_s, seed, burn, record=rec)
-    M2_o = ti.m2_from_integral(float(np.dot(ti.simpson_weights(L), means_o)), eps)
+    f = ti.energy_table(psi_np, eps, sector) if N <= 12 else ti.energy_fn(psi_np, eps)
+    means_o, _ = ti.metropolis_means(f, N, L, n_s, seed, burn, record=rec, sector=sector)
+    M2_o = ti.m2_from_integral(float(np.dot(ti.simpson_weights(L), means_o)), eps, sector)
     T = burn + n_s
     assert traj.shape == (L, T)
     parted = []
@@ -56,8 +66,10 @@ def check_against_oracle(psi_np, L, n_s, burn, seed, eps=0.0):
         assert rec["margin"][l, t0] < DELTA, (l, t0, rec["margin"][l, t0])
         r = oracle.splitmix64(seed + l, 1 + 2 * T)
         a = int(rec["traj"][l, t0 - 1]) if t0 > 0 else int(r[0] >> np.uint64(64 - N))
+        if t0 == 0 and sector == "even" and bin(a).count("1") % 2:
+            a ^= 1
         for t in range(t0, T):
-            flip = a ^ (1 << int(r[1 + 2 * t] % np.uint64(N)))
+            flip = a ^ move_mask(r[1 + 2 * t], N, sector)
             assert traj[l, t] in (a, flip), (l, t)
             a = int(traj[l, t])
         parted.append(l)
@@ -89,6 +101,26 @@ def test_edge_cases():
     check_against_oracle(I.zero_state(6).astype(np.complex64), 5, 300, 10, 1, eps=1e-3)
     check_against_oracle(I.ghz_state(6).astype(np.complex64), 3, 300, 0, 8, eps=1e-1)
     check_against_oracle(I.t_state_product(7).astype(np.complex64), 8, 300, 10, 4, eps=1e-2)
+
+
+@pytest.mark.parametrize("label", ["u1_N10", "z2_N13", "u1_N16", "u1_N9_eps", "N2"])
+def test_even_sector_chains_follow_the_oracle(label):
+    # Sec. 3.2: chains restricted to even-weight X-strings for U(1) / prod Z symmetric states
+    psi, L, n_s, burn, seed, eps = {
+        "u1_N10": (I.u1_state(10, 5, 3601, dtype=np.complex64), 5, 300, 10, 3, 0.0),
+        "z2_N13": (I.parity_state(13, 3602, dtype=np.complex64), 4, 200, 0, 8, 0.0),
+        "u1_N16": (I.u1_state(16, 8, 3603, dtype=np.complex64), 3, 100, 5, 21, 0.0),
+        "u1_N9_eps": (I.u1_state(9, 3, 3604, dtype=np.complex64), 4, 200, 5, 4, 1e-3),  # off half filling
+        "N2": (I.parity_state(2, 3605, dtype=np.complex64), 3, 100, 0, 2 ** 64 - 1, 0.0),
+    }[label]
+    check_against_oracle(psi, L, n_s, burn, seed, eps, sector="even")
+
+
+def test_even_sector_invalid_for_one_qubit():
+    psi = torch.from_numpy(I.parity_state(1, 1, dtype=np.complex64)).to(DEV)
+    with pytest.raises(hm.HadamagError) as e:
+        hm.sre_ti(psi, 3, 10, 1, even_sector=True)
+    assert e.value.code == 1
 
 
 def test_complex128_input_and_unrecorded_run():
