@@ -129,3 +129,39 @@ def test_planted_convention_mistake_fails():
     for leg in range(2):
         v = np.einsum("ua,bam->bum", Mbad, v.reshape(-1, 9, 9 ** (1 - leg))).reshape(-1)
     assert not np.allclose(v / 9, brute.wigner_mixed_brute(rho), atol=1e-6)
+
+
+def _shift_gather_chi(rho):
+    """chi_b(a) from v_x = rho[-x - a, x - a] (digit-wise mod 3) and F_3^{(x)N}: the route the
+    mixed-state kernels take instead of Algorithm 6's leg sweep (restated here in NumPy)."""
+    D = rho.shape[0]
+    N = mixed._n_sites(D)
+    d = np.stack([(np.arange(D) // 3 ** k) % 3 for k in range(N)], axis=1)
+    pw = 3 ** np.arange(N)
+    r = (((-d[None, :, :] - d[:, None, :]) % 3) * pw).sum(-1)  # [a, x]
+    c = (((d[None, :, :] - d[:, None, :]) % 3) * pw).sum(-1)
+    w = np.exp(2j * np.pi / 3)
+    F = np.array([[w ** (2 * j * k) for k in range(3)] for j in range(3)])
+    t = rho[r, c].reshape((D,) + (3,) * N)  # axis 1 + k: digit N-1-k of x
+    for ax in range(1, N + 1):
+        t = np.moveaxis(np.tensordot(F, t, axes=([1], [ax])), 0, ax)
+    return t.reshape(D, D), r, c
+
+
+@pytest.mark.parametrize("N", [1, 2, 3])
+def test_shift_gather_reproduces_algorithm_6(N):
+    # (a, x) -> (-x - a, x - a) reads every entry of rho once; the transformed values are
+    # 3^N W_u up to the labelling of u, real for Hermitian rho
+    for rank in (1, 2, 3 ** N):
+        rho = random_rho(N, 300 + 10 * N + rank, rank)
+        chi, r, c = _shift_gather_chi(rho)
+        flat = np.sort((r * 3 ** N + c).ravel())
+        np.testing.assert_array_equal(flat, np.arange(9 ** N))
+        assert np.abs(chi.imag).max() < 1e-13
+        W = mixed.wigner_mixed(rho).real
+        np.testing.assert_allclose(np.sort(np.abs(chi.real).ravel()) / 3 ** N, np.sort(np.abs(W)), atol=1e-14)
+        assert np.log2(np.abs(chi.real).sum() / 3 ** N) == pytest.approx(mixed.mana_mixed(rho)[0], abs=1e-12)
+    # on rho = |psi><psi| the route gives the C oracle's Algorithm 5 mana
+    psi = I.gaussian_state(N, 330 + N, d=3)
+    chi, _, _ = _shift_gather_chi(np.outer(psi, psi.conj()))
+    assert np.log2(np.abs(chi.real).sum() / 3 ** N) == pytest.approx(oracle.mana(psi)[0], abs=1e-12)
