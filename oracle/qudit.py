@@ -1,0 +1,173 @@
+"""Mana of qudits of odd prime dimension d, FP64 NumPy.  TEST INFRASTRUCTURE ONLY: only
+`tests/` may import this module.
+
+Sec. 2 defines the Heisenberg-Weyl operators, phase-space point operators and mana for
+qutrits and notes that the construction applies to any odd prime d:
+    X|k> = |k+1>,  Z|k> = w^k |k>  (w = e^{2 pi i / d}),  T_ab = w^{-2^{-1} ab} Z^a X^b,
+    A_0 = d^-N sum_u T_u,  A_u = T_u A_0 T_u^dag,  W(u) = tr(A_u rho) / d^N,
+    mana = log2 sum_u |W(u)|.
+Two independent evaluations:
+  * `wigner_brute`: the definition with every T_u and A_u built as a dense matrix (tiny N);
+  * `mana_fast`: Algorithm 5's per-shift transform for general d.  With
+    A_{ab}|x> = w^{2a(b-x)} |2b - x> (from the definitions above), <psi|A_ab|psi> =
+    sum_y w^{-2ay} psi_{b+y} conj(psi_{b-y}); for every shift a (digit-wise mod d)
+        v_x = conj(psi_{x-a}) psi_{-x-a},   chi = F_d^{(x)N} v,  (F_d)_{jk} = w^{2jk},
+    and the values chi / d^N are the W(u) (a relabelling of u); chi is real for pure states.
+Sites: site j = base-d digit j of the index (least significant first).
+"""
+from __future__ import annotations
+
+import itertools
+
+import numpy as np
+
+PRIMES = (3, 5, 7, 11, 13)
+
+
+def _check_d(d: int):
+    if d not in PRIMES:
+        raise ValueError(f"d must be an odd prime in {PRIMES}")
+
+
+def n_sites(dim: int, d: int) -> int:
+    N = 0
+    while d ** N < dim:
+        N += 1
+    if d ** N != dim:
+        raise ValueError(f"dimension must be {d}^N")
+    return N
+
+
+def hw_operator(a: int, b: int, d: int) -> np.ndarray:
+    """T_ab = w^{-2^{-1} ab} Z^a X^b for one qudit."""
+    _check_d(d)
+    w = np.exp(2j * np.pi / d)
+    X = np.roll(np.eye(d, dtype=np.complex128), 1, axis=0)
+    Z = np.diag([w ** k for k in range(d)])
+    two_inv = (d + 1) // 2
+    return (w ** (-(two_inv * a * b) % d)) * (np.linalg.matrix_power(Z, a) @ np.linalg.matrix_power(X, b))
+
+
+def _kron_sites(mats):
+    out = np.array([[1.0 + 0j]])
+    for m in mats:
+        out = np.kron(m, out)  # later sites are more significant
+    return out
+
+
+def phase_point_operators(N: int, d: int):
+    """All d^(2N) phase-space point operators A_u (list, u = per-site (a, b) in row-major order)."""
+    singles = {(a, b): hw_operator(a, b, d) for a in range(d) for b in range(d)}
+    us = list(itertools.product(range(d * d), repeat=N))
+    Ts = [_kron_sites([singles[divmod(k, d)] for k in u]) for u in us]
+    A0 = sum(Ts) / d ** N
+    return [T @ A0 @ T.conj().T for T in Ts], A0
+
+
+def wigner_brute(psi, d: int) -> np.ndarray:
+    """W(u) = <psi|A_u|psi> / d^N from dense operators (N small)."""
+    psi = np.asarray(psi, dtype=np.complex128)
+    N = n_sites(psi.size, d)
+    As, _ = phase_point_operators(N, d)
+    return np.array([np.vdot(psi, A @ psi) for A in As]) / d ** N
+
+
+def mana_brute(psi, d: int):
+    W = wigner_brute(psi, d)
+    s = float(np.abs(W.real).sum())
+    return float(np.log2(s)), s
+
+
+def chi_fast(psi, d: int, chunk: int = 256) -> np.ndarray:
+    """chi[a, b] for every shift a and frequency b (both base-d indices)."""
+    _check_d(d)
+    psi = np.asarray(psi, dtype=np.complex128)
+    N = n_sites(psi.size, d)
+    D = psi.size
+    dig = np.stack([(np.arange(D) // d ** k) % d for k in range(N)], axis=1)  # [index, site]
+    pw = d ** np.arange(N)
+    w = np.exp(2j * np.pi / d)
+    F = np.array([[w ** ((2 * j * k) % d) for k in range(d)] for j in range(d)])
+    out = np.empty((D, D), dtype=np.complex128)
+    for a0 in range(0, D, chunk):
+        da = dig[a0:a0 + chunk]  # [a, site]
+        i1 = (((dig[None, :, :] - da[:, None, :]) % d) * pw).sum(-1)   # x - a
+        i2 = (((-dig[None, :, :] - da[:, None, :]) % d) * pw).sum(-1)  # -x - a
+        v = np.conj(psi[i1]) * psi[i2]
+        t = v.reshape((v.shape[0],) + (d,) * N)  # axis 1 + k holds site N-1-k
+        for ax in range(1, N + 1):
+            t = np.moveaxis(np.tensordot(F, t, axes=([1], [ax])), 0, ax)
+        out[a0:a0 + chunk] = t.reshape(v.shape[0], D)
+    return out
+
+
+def mana_fast(psi, d: int):
+    """(mana in bits, sum |W|, sum W, sum W^2) by the per-shift transform."""
+    psi = np.asarray(psi, dtype=np.complex128)
+    N = n_sites(psi.size, d)
+    chi = chi_fast(psi, d).real / d ** N
+    s = float(np.abs(chi).sum())
+    return float(np.log2(s)), s, float(chi.sum()), float((chi ** 2).sum())
+
+
+# ---- qudit states used by the pins ------------------------------------------------------
+
+def zero_state(N: int, d: int) -> np.ndarray:
+    v = np.zeros(d ** N, dtype=np.complex128)
+    v[0] = 1.0
+    return v
+
+
+def ghz(N: int, d: int) -> np.ndarray:
+    """sum_k |k...k> / sqrt d, a stabilizer state."""
+    v = np.zeros(d ** N, dtype=np.complex128)
+    ones = sum(d ** j for j in range(N))
+    for k in range(d):
+        v[k * ones] = 1.0 / np.sqrt(d)
+    return v
+
+
+def graph_state(N: int, d: int, edges) -> np.ndarray:
+    """prod CZ_ij |+>^N with CZ|x, y> = w^{xy}|x, y>, a stabilizer state."""
+    D = d ** N
+    dig = np.stack([(np.arange(D) // d ** k) % d for k in range(N)], axis=1)
+    ph = np.zeros(D, dtype=np.int64)
+    for i, j in edges:
+        ph += dig[:, i] * dig[:, j]
+    return np.exp(2j * np.pi * (ph % d) / d) / np.sqrt(D)
+
+
+def apply_1site(psi, U, q: int, N: int, d: int) -> np.ndarray:
+    t = np.asarray(psi, dtype=np.complex128).reshape((d,) * N)
+    ax = N - 1 - q
+    return np.moveaxis(np.tensordot(U, t, axes=([1], [ax])), 0, ax).reshape(-1)
+
+
+def sum_gate(psi, c: int, t: int, N: int, d: int) -> np.ndarray:
+    """|x_c, x_t> -> |x_c, x_t + x_c>."""
+    D = d ** N
+    idx = np.arange(D)
+    xc, xt = (idx // d ** c) % d, (idx // d ** t) % d
+    dst = idx + (((xt + xc) % d) - xt) * d ** t
+    out = np.zeros(D, dtype=np.complex128)
+    out[dst] = np.asarray(psi, dtype=np.complex128)
+    return out
+
+
+def random_clifford_circuit(psi, N: int, d: int, n_gates: int, seed: int) -> np.ndarray:
+    """Random gates from {Fourier F_{xy} = w^{xy}/sqrt d, phase w^{x^2}, X, SUM} (all Clifford
+    for odd prime d)."""
+    rng = np.random.default_rng(seed)
+    w = np.exp(2j * np.pi / d)
+    F = np.array([[w ** ((x * y) % d) for y in range(d)] for x in range(d)]) / np.sqrt(d)
+    P = np.diag([w ** ((x * x) % d) for x in range(d)])
+    X = np.roll(np.eye(d), 1, axis=0)
+    out = np.asarray(psi, dtype=np.complex128)
+    for _ in range(n_gates):
+        g = int(rng.integers(4))
+        if g < 3 or N == 1:
+            out = apply_1site(out, (F, P, X)[g % 3], int(rng.integers(N)), N, d)
+        else:
+            c, t = rng.choice(N, 2, replace=False)
+            out = sum_gate(out, int(c), int(t), N, d)
+    return out

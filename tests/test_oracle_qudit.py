@@ -1,0 +1,84 @@
+"""Pins of the odd-prime-qudit mana oracle (Sec. 2, the remark that the qutrit construction
+applies to any odd prime d) on the CPU: the per-shift transform against the dense definition
+(every A_u built explicitly), the qutrit C oracle at d = 3, the Wigner sum rules, zeros on
+stabilizer states, additivity, Clifford invariance and a planted mistake."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import qudit as Q
+from paper_2601_07824_gb300 import inputs as I
+
+
+@pytest.mark.parametrize("d,N", [(3, 1), (3, 2), (5, 1), (5, 2), (7, 1), (7, 2), (11, 1), (13, 1)])
+def test_fast_transform_equals_dense_definition(d, N):
+    psi = I.gaussian_state(N, 10 * d + N, d=d)
+    W = Q.wigner_brute(psi, d)
+    assert np.abs(W.imag).max() < 1e-14
+    chi = Q.chi_fast(psi, d)
+    assert np.abs(chi.imag).max() < 1e-12
+    np.testing.assert_allclose(np.sort(np.abs(chi.real).ravel()) / d ** N, np.sort(np.abs(W.real)), atol=1e-14)
+    m, s, s1, s2 = Q.mana_fast(psi, d)
+    mb, sb = Q.mana_brute(psi, d)
+    assert m == pytest.approx(mb, abs=1e-12) and s == pytest.approx(sb, rel=1e-12)
+
+
+@pytest.mark.parametrize("N", [1, 2, 3, 4])
+def test_qutrits_agree_with_the_c_oracle(N):
+    psi = I.gaussian_state(N, 500 + N, d=3)
+    assert Q.mana_fast(psi, 3)[0] == pytest.approx(oracle.mana(psi)[0], abs=1e-12)
+
+
+@pytest.mark.parametrize("d,N", [(5, 3), (7, 2), (11, 2), (13, 2)])
+def test_sum_rules(d, N):
+    psi = I.gaussian_state(N, 600 + d + N, d=d)
+    _, s, s1, s2 = Q.mana_fast(psi, d)
+    assert s1 == pytest.approx(1.0, abs=1e-12)            # sum_u W(u) = tr rho
+    assert s2 == pytest.approx(d ** -N, rel=1e-10)         # sum_u W(u)^2 = tr rho^2 / d^N
+    assert s >= 1.0 - 1e-12
+
+
+@pytest.mark.parametrize("d,N", [(5, 1), (5, 3), (7, 2), (11, 2)])
+def test_stabilizer_states_have_zero_mana(d, N):
+    states = [Q.zero_state(N, d), Q.ghz(N, d)]
+    if N >= 2:
+        states.append(Q.graph_state(N, d, [(j, j + 1) for j in range(N - 1)]))
+    states.append(Q.random_clifford_circuit(Q.zero_state(N, d), N, d, 25, seed=7 * d + N))
+    for psi in states:
+        assert np.linalg.norm(psi) == pytest.approx(1.0, abs=1e-12)
+        m, s, _, _ = Q.mana_fast(psi, d)
+        assert abs(m) < 1e-12, (d, N)
+        W = Q.chi_fast(psi, d).real / d ** N
+        assert W.min() > -1e-13  # Hudson: non-negative Wigner function
+
+
+@pytest.mark.parametrize("d", [5, 7])
+def test_additivity_and_clifford_invariance(d):
+    a, b = I.gaussian_state(1, 70 + d, d=d), I.gaussian_state(2, 71 + d, d=d)
+    ab = np.kron(b, a)  # a on site 0, b on sites 1, 2
+    assert Q.mana_fast(ab, d)[0] == pytest.approx(Q.mana_fast(a, d)[0] + Q.mana_fast(b, d)[0], abs=1e-12)
+    psi = I.gaussian_state(2, 72 + d, d=d)
+    c = Q.random_clifford_circuit(psi, 2, d, 30, seed=d)
+    assert Q.mana_fast(c, d)[0] == pytest.approx(Q.mana_fast(psi, d)[0], abs=1e-11)
+
+
+def test_planted_mistake_fails():
+    # a dropped conjugate in v_x breaks the match with the dense definition
+    d, N = 5, 2
+    psi = I.gaussian_state(N, 80, d=d)
+    W = Q.wigner_brute(psi, d).real
+    D = psi.size
+    dig = np.stack([(np.arange(D) // d ** k) % d for k in range(N)], axis=1)
+    pw = d ** np.arange(N)
+    w = np.exp(2j * np.pi / d)
+    F = np.array([[w ** ((2 * j * k) % d) for k in range(d)] for j in range(d)])
+    vals = []
+    for a in range(D):
+        i1 = (((dig - dig[a]) % d) * pw).sum(-1)
+        i2 = (((-dig - dig[a]) % d) * pw).sum(-1)
+        t = (psi[i1] * psi[i2]).reshape((d,) * N)
+        for ax in range(N):
+            t = np.moveaxis(np.tensordot(F, t, axes=([1], [ax])), 0, ax)
+        vals.append(np.abs(t.ravel()))
+    bad = np.sort(np.concatenate(vals)) / d ** N
+    assert not np.allclose(bad, np.sort(np.abs(W)), atol=1e-6)
