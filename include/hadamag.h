@@ -189,6 +189,21 @@ hadamag_status hadamag_mana_sums(hadamag_ctx_t ctx, const void* psi_dev, int N, 
                                  double* sums_out, hadamag_stream_t stream);
 
 /*
+ * Mana of N qudits of odd prime dimension d, Sec. 2 (the qutrit construction holds for any odd
+ * prime d): with w = e^{2 pi i / d}, T_ab = w^{-2^{-1} ab} Z^a X^b, A_0 = d^-N sum_u T_u,
+ * A_u = T_u A_0 T_u^dag and W(u) = <psi|A_u|psi> / d^N,  mana = log2 sum_u |W(u)|.
+ * Algorithm 5 generalised: for every shift a, v_x = conj(psi_{x-a}) psi_{-x-a} (digit-wise
+ * mod d), chi = F_d^{(x)N} v with (F_d)_jk = w^{2jk}, W = chi / d^N (a relabelling of u).
+ * psi_dev: d^N amplitudes, qudit j = base-d digit j.  d = 3 (1 <= N <= 13, the hadamag_mana
+ * kernels), 5 (N <= 6), 7 (N <= 5), 11 (N <= 4), 13 (N <= 3); other d give UNSUPPORTED.
+ * sums_out (3 host doubles or NULL): [sum |chi|, sum chi, sum chi^2] over all (a, b).
+ * Synchronises `stream`.
+ */
+hadamag_status hadamag_mana_qudit(hadamag_ctx_t ctx, const void* psi_dev, int N, int d,
+                                  hadamag_dtype dtype, double* mana_out, double* sums_out,
+                                  hadamag_stream_t stream);
+
+/*
  * Mana of an N-qutrit density matrix, Sec. 3.3.3 (Algorithm 6; Eq. mana with
  * W_u = tr(rho A_u) / 3^N over the phase-space point operators A_u):
  *     mana = log2 sum_u |W_u|  (bits; 0 for stabilizer mixtures, equal to hadamag_mana on pure states).

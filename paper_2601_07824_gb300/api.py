@@ -172,6 +172,20 @@ def mana(psi: torch.Tensor):
     return m.value, sw.value
 
 
+def mana_qudit(psi: torch.Tensor, d: int):
+    """(mana in bits, [sum |chi|, sum chi, sum chi^2]) of N qudits of odd prime dimension d
+    (d^N amplitudes; Sec. 2's construction for general odd prime d, Algorithm 5 generalised)."""
+    if int(d) < 2:
+        raise ValueError("d must be an odd prime")
+    N = _check_state(psi, int(d))
+    c = _ctx(psi)
+    m = ctypes.c_double()
+    sums = (ctypes.c_double * 3)()
+    c.check(c.lib.hadamag_mana_qudit(c.h, ctypes.c_void_p(psi.data_ptr()), N, int(d), _dtype_code(psi),
+                                     ctypes.byref(m), sums, _stream(psi)), "hadamag_mana_qudit")
+    return m.value, list(sums)
+
+
 def mana_mixed(rho: torch.Tensor):
     """(mana in bits, [sum |chi|, sum chi, sum chi^2]) of an N-qutrit density matrix given as a
     3^N x 3^N CUDA tensor (Algorithm 6's W via the Algorithm 5 transform, Sec. 3.3.3)."""

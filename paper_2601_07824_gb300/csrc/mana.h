@@ -30,4 +30,10 @@ cudaError_t launch_mana_onepass(const float2* src, int N, bool mixed, double* ou
 cudaError_t mana_twopass_grid(int N, bool mixed, int sm_count, int* grid);
 cudaError_t launch_mana_twopass(const ManaParams& P, bool mixed, int grid, cudaStream_t st);
 
+// Odd-prime qudits d = 5, 7, 11, 13 (qudit.cu): largest N with d^N <= 25600 (0 for other d),
+// and the launch writing grid <= max_grid per-CTA triples [sum |chi|, sum chi, sum chi^2].
+int mana_qudit_max_n(int d);
+cudaError_t launch_mana_qudit(const float2* psi, int N, int d, double* out, int sm_count, int max_grid, int* grid,
+                              cudaStream_t st);
+
 }  // namespace hm

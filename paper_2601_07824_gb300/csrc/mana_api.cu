@@ -103,6 +103,46 @@ extern "C" hadamag_status hadamag_mana_sums(hadamag_ctx_t c, const void* psi, in
     return mana_sums(c, psi, N, dt, reinterpret_cast<cudaStream_t>(stream), sums_out, false);
 }
 
+extern "C" hadamag_status hadamag_mana_qudit(hadamag_ctx_t c, const void* psi, int N, int d, hadamag_dtype dt,
+                                             double* mana_out, double* sums_out, hadamag_stream_t stream) {
+    if (!c) return HADAMAG_ERR_INVALID_ARG;
+    if (!aligned16(psi)) return fail(c, HADAMAG_ERR_INVALID_ARG, "null or misaligned pointer");
+    if (dt != HADAMAG_C64 && dt != HADAMAG_C128) return fail(c, HADAMAG_ERR_INVALID_ARG, "bad dtype");
+    const int nmax = d == 3 ? 13 : mana_qudit_max_n(d);
+    if (nmax == 0) return fail(c, HADAMAG_ERR_UNSUPPORTED, "d must be 3, 5, 7, 11 or 13 (got %d)", d);
+    if (N < 1 || N > nmax) return fail(c, HADAMAG_ERR_INVALID_ARG, "N must be in [1, %d] for d = %d (got %d)", nmax, d, N);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    double sums[3];
+    hadamag_status s;
+    int64_t dim = 1;
+    for (int j = 0; j < N; ++j) dim *= d;
+    if (d == 3) {
+        if ((s = mana_sums(c, psi, N, dt, st, sums, false))) return s;
+    } else {
+        cudaError_t e;
+        if ((s = begin(c, st))) return s;
+        const float2* p;
+        if ((s = as_c64(c, psi, dim, dt, st, &p))) return s;
+        const int max_grid = c->sm_count * 8;
+        if ((s = ensure_buf(c, c->part, (size_t)max_grid * 3 * sizeof(double)))) return s;
+        int grid = 0;
+        e = launch_mana_qudit(p, N, d, (double*)c->part.ptr, c->sm_count, max_grid, &grid, st);
+        c->launches++;
+        if (e != cudaSuccess) return cuda_fail(c, e, "mana_qudit");
+        e = launch_sum_triples((const double*)c->part.ptr, grid, (double*)c->res.ptr, st);
+        c->launches++;
+        if (e != cudaSuccess) return cuda_fail(c, e, "sum_triples");
+        if ((s = finish(c, (const double*)c->res.ptr, 3, st))) return s;
+        sums[0] = c->host_res[0]; sums[1] = c->host_res[1]; sums[2] = c->host_res[2];
+    }
+    double m = std::log2(sums[0] / (double)dim);  // sum_u |W(u)|, W = chi / d^N
+    if (m == 0.0) m = 0.0;
+    if (mana_out) *mana_out = m;
+    if (sums_out) { sums_out[0] = sums[0]; sums_out[1] = sums[1]; sums_out[2] = sums[2]; }
+    if (!std::isfinite(m)) return fail(c, HADAMAG_ERR_NONFINITE, "non-finite mana");
+    return HADAMAG_OK;
+}
+
 extern "C" hadamag_status hadamag_mana_mixed(hadamag_ctx_t c, const void* rho, int N, hadamag_dtype dt,
                                              double* mana_out, double* sums_out, hadamag_stream_t stream) {
     if (!c) return HADAMAG_ERR_INVALID_ARG;

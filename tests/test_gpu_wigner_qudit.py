@@ -1,0 +1,89 @@
+"""Mana of odd-prime qudits (Sec. 2's construction for any odd prime d; Algorithm 5
+generalised) on the GPU against the FP64 oracle (`oracle/qudit.py`, pinned to the dense
+definition), the Wigner sum rules and zeros on stabilizer states.
+
+Tolerances as for qutrit mana: generic states 1e-6 max(1, |mana|); stabilizer states carry
+FP32 residue in their exact zeros, bounded by 4 * d^(N/2) * 2^-24 / ln 2 + 1e-7."""
+import ctypes
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import qudit as Q
+from paper_2601_07824_gb300 import inputs as I
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2601_07824_gb300 as hm  # noqa: E402
+from paper_2601_07824_gb300 import _lib  # noqa: E402
+
+DEV = torch.device("cuda:0")
+CASES = [(5, n) for n in range(1, 7)] + [(7, n) for n in range(1, 6)] + [(11, n) for n in range(1, 5)] + \
+        [(13, n) for n in range(1, 4)]
+
+
+def on_dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(DEV)
+
+
+def stab_tol(d, N):
+    return 4 * d ** (N / 2) * 2.0 ** -24 / math.log(2) + 1e-7
+
+
+@pytest.mark.parametrize("d,N", CASES)
+def test_gaussian_states_vs_oracle(d, N):
+    psi = I.gaussian_state(N, 1000 * d + N, d=d, dtype=np.complex64)
+    m, sums = hm.mana_qudit(on_dev(psi), d)
+    mo, so, s1, s2 = Q.mana_fast(psi, d)
+    assert abs(m - mo) <= 1e-6 * max(1.0, abs(mo)), (d, N, m, mo)
+    assert abs(sums[0] / d ** N - so) <= 1e-6 * so
+    assert abs(sums[1] / d ** N - 1.0) < 1e-5  # sum_u W(u) = 1
+    assert abs(sums[2] / d ** N - 1.0) < 1e-5  # sum_u W(u)^2 = d^-N
+
+
+def test_qutrits_take_the_qutrit_kernels():
+    psi = I.gaussian_state(7, 1700, d=3, dtype=np.complex64)
+    m, _ = hm.mana_qudit(on_dev(psi), 3)
+    assert m == hm.mana(on_dev(psi))[0]
+    assert abs(m - oracle.mana(psi)[0]) <= 1e-6 * max(1.0, abs(m))
+
+
+@pytest.mark.parametrize("d,N", [(5, 4), (7, 3), (11, 2), (13, 2)])
+def test_stabilizer_states_have_zero_mana(d, N):
+    states = [Q.zero_state(N, d), Q.ghz(N, d), Q.graph_state(N, d, [(j, j + 1) for j in range(N - 1)]),
+              Q.random_clifford_circuit(Q.zero_state(N, d), N, d, 30, seed=d * 10 + N)]
+    for psi in states:
+        m, _ = hm.mana_qudit(on_dev(psi.astype(np.complex64)), d)
+        assert abs(m) <= stab_tol(d, N), (d, N, m)
+
+
+def test_complex128_input():
+    psi = I.gaussian_state(4, 1800, d=5)
+    m128, _ = hm.mana_qudit(on_dev(psi), 5)
+    m64, _ = hm.mana_qudit(on_dev(psi.astype(np.complex64)), 5)
+    assert m128 == m64  # complex128 is rounded to complex64 on the device first
+    assert abs(m128 - Q.mana_fast(psi, 5)[0]) <= 1e-6 * max(1.0, abs(m128))
+
+
+def test_invalid_arguments():
+    lib = _lib.load()
+    c = hm.context(0)
+    m = ctypes.c_double()
+    stream = ctypes.c_void_p(torch.cuda.current_stream(DEV).cuda_stream)
+    buf = torch.zeros(5 ** 7, dtype=torch.complex64, device=DEV)
+    buf[0] = 1.0
+    ptr = ctypes.c_void_p(buf.data_ptr())
+    assert lib.hadamag_mana_qudit(c.h, ptr, 2, 9, 0, ctypes.byref(m), None, stream) == 2   # d not an odd prime
+    assert lib.hadamag_mana_qudit(c.h, ptr, 2, 4, 0, ctypes.byref(m), None, stream) == 2
+    assert lib.hadamag_mana_qudit(c.h, ptr, 7, 5, 0, ctypes.byref(m), None, stream) == 1   # 5^7 > 25600
+    assert lib.hadamag_mana_qudit(c.h, ptr, 0, 5, 0, ctypes.byref(m), None, stream) == 1
+    with pytest.raises(ValueError):
+        hm.mana_qudit(buf[:24].contiguous(), 5)
+    # the context stays usable: |0...0> of 6 qudits has mana 0
+    assert abs(hm.mana_qudit(buf[:5 ** 6].contiguous(), 5)[0]) <= stab_tol(5, 6)
