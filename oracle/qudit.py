@@ -78,27 +78,62 @@ def mana_brute(psi, d: int):
     return float(np.log2(s)), s
 
 
+def _digits(D: int, N: int, d: int) -> np.ndarray:
+    return np.stack([(np.arange(D) // d ** k) % d for k in range(N)], axis=1)  # [index, site]
+
+
+def _transform_rows(V: np.ndarray, d: int, N: int) -> np.ndarray:
+    """F_d^{(x)N} applied to every row of V, (F_d)_{jk} = w^{2jk}."""
+    w = np.exp(2j * np.pi / d)
+    F = np.array([[w ** ((2 * j * k) % d) for k in range(d)] for j in range(d)])
+    t = V.reshape((V.shape[0],) + (d,) * N)  # axis 1 + k holds site N-1-k
+    for ax in range(1, N + 1):
+        t = np.moveaxis(np.tensordot(F, t, axes=([1], [ax])), 0, ax)
+    return t.reshape(V.shape[0], -1)
+
+
+def _shift_indices(dig: np.ndarray, da: np.ndarray, d: int, pw: np.ndarray):
+    """idx(x - a) and idx(-x - a) (digit-wise mod d) for the shifts in da and every x."""
+    i1 = (((dig[None, :, :] - da[:, None, :]) % d) * pw).sum(-1)
+    i2 = (((-dig[None, :, :] - da[:, None, :]) % d) * pw).sum(-1)
+    return i1, i2
+
+
 def chi_fast(psi, d: int, chunk: int = 256) -> np.ndarray:
     """chi[a, b] for every shift a and frequency b (both base-d indices)."""
     _check_d(d)
     psi = np.asarray(psi, dtype=np.complex128)
     N = n_sites(psi.size, d)
     D = psi.size
-    dig = np.stack([(np.arange(D) // d ** k) % d for k in range(N)], axis=1)  # [index, site]
-    pw = d ** np.arange(N)
-    w = np.exp(2j * np.pi / d)
-    F = np.array([[w ** ((2 * j * k) % d) for k in range(d)] for j in range(d)])
+    dig, pw = _digits(D, N, d), d ** np.arange(N)
     out = np.empty((D, D), dtype=np.complex128)
     for a0 in range(0, D, chunk):
-        da = dig[a0:a0 + chunk]  # [a, site]
-        i1 = (((dig[None, :, :] - da[:, None, :]) % d) * pw).sum(-1)   # x - a
-        i2 = (((-dig[None, :, :] - da[:, None, :]) % d) * pw).sum(-1)  # -x - a
-        v = np.conj(psi[i1]) * psi[i2]
-        t = v.reshape((v.shape[0],) + (d,) * N)  # axis 1 + k holds site N-1-k
-        for ax in range(1, N + 1):
-            t = np.moveaxis(np.tensordot(F, t, axes=([1], [ax])), 0, ax)
-        out[a0:a0 + chunk] = t.reshape(v.shape[0], D)
+        i1, i2 = _shift_indices(dig, dig[a0:a0 + chunk], d, pw)
+        out[a0:a0 + chunk] = _transform_rows(np.conj(psi[i1]) * psi[i2], d, N)
     return out
+
+
+def mana_grad(psi, d: int, chunk: int = 256):
+    """(mana, d mana / d psi*) on the unnormalised psi (Wirtinger gradient; mana =
+    log2(sum_{a,b} |chi_b(a)| / d^N)).  From v_x = conj(psi_{x-a}) psi_{-x-a}:
+        d chi_b(a) / d psi*_w = d conj(chi_b(a)) / d psi*_w = F_{b, w+a} psi_{-w-2a},
+    so with y = w + a and G_a = F_d^{(x)N} (Re chi_a / |chi_a|) (F_d symmetric)
+        d m / d psi*_{y-a} += psi_{-y-a} G_a(y),   d mana / d psi* = (d m / d psi*) / (m ln 2).
+    Defined where no chi_b(a) vanishes (not on stabilizer states)."""
+    _check_d(d)
+    psi = np.asarray(psi, dtype=np.complex128)
+    N = n_sites(psi.size, d)
+    D = psi.size
+    dig, pw = _digits(D, N, d), d ** np.arange(N)
+    g = np.zeros(D, dtype=np.complex128)
+    m = 0.0
+    for a0 in range(0, D, chunk):
+        i1, i2 = _shift_indices(dig, dig[a0:a0 + chunk], d, pw)  # i1 = idx(y - a), i2 = idx(-y - a)
+        chi = _transform_rows(np.conj(psi[i1]) * psi[i2], d, N)
+        m += float(np.abs(chi).sum())
+        G = _transform_rows(chi.real / np.abs(chi), d, N)
+        np.add.at(g, i1.ravel(), (psi[i2] * G).ravel())
+    return float(np.log2(m / d ** N)), g / (m * np.log(2.0))
 
 
 def mana_fast(psi, d: int):

@@ -82,3 +82,34 @@ def test_planted_mistake_fails():
         vals.append(np.abs(t.ravel()))
     bad = np.sort(np.concatenate(vals)) / d ** N
     assert not np.allclose(bad, np.sort(np.abs(W)), atol=1e-6)
+
+
+# ---- gradient of the mana ---------------------------------------------------------------
+
+@pytest.mark.parametrize("d,N", [(3, 1), (3, 2), (3, 4), (5, 2), (7, 2)])
+def test_mana_gradient_matches_finite_differences(d, N):
+    rng = np.random.default_rng(90 + d + N)
+    psi = I.gaussian_state(N, 91 + d + N, d=d) * 1.3  # unnormalised on purpose
+    m, g = Q.mana_grad(psi, d)
+    # mana of the vector as given (sum |chi| scales as |psi|^4)
+    assert m == pytest.approx(Q.mana_fast(psi, d)[0], abs=1e-12)
+    mf = lambda v: float(np.log2(np.abs(Q.chi_fast(v, d)).sum() / d ** N))  # noqa: E731
+    h = 1e-6
+    for _ in range(4):
+        delta = rng.normal(size=psi.size) + 1j * rng.normal(size=psi.size)
+        fd = (mf(psi + h * delta) - mf(psi - h * delta)) / (2 * h)
+        assert fd == pytest.approx(2 * np.real(np.vdot(g, delta)), rel=1e-5, abs=1e-8)
+    if d == 3:  # the independent C oracle (Algorithm 5) gives the same finite differences
+        delta = rng.normal(size=psi.size) + 1j * rng.normal(size=psi.size)
+        fd = (oracle.mana(psi + h * delta)[0] - oracle.mana(psi - h * delta)[0]) / (2 * h)
+        assert fd == pytest.approx(2 * np.real(np.vdot(g, delta)), rel=1e-5, abs=1e-8)
+
+
+@pytest.mark.parametrize("d,N", [(3, 3), (5, 2)])
+def test_mana_gradient_phase_and_scale_identities(d, N):
+    psi = I.gaussian_state(N, 95 + d, d=d) * 0.7
+    _, g = Q.mana_grad(psi, d)
+    # a global phase does not change mana: Im sum conj(g) psi = 0
+    assert abs(np.imag(np.vdot(g, psi))) < 1e-12
+    # mana(c psi) = mana(psi) + 2 log2 c: 2 Re sum conj(g) psi = 2 / ln 2
+    assert 2 * np.real(np.vdot(g, psi)) == pytest.approx(2 / np.log(2.0), rel=1e-12)
