@@ -204,6 +204,21 @@ hadamag_status hadamag_mana_qudit(hadamag_ctx_t ctx, const void* psi_dev, int N,
                                   hadamag_stream_t stream);
 
 /*
+ * Mana and its Wirtinger gradient d mana / d psi* for N qudits of odd prime dimension d (not in
+ * the paper; the analogue of hadamag_sre_grad for Eq. mana2).  With chi as in hadamag_mana_qudit
+ * and m = sum_{a,b} |chi_b(a)|:  d chi_b(a) / d psi*_w = d conj(chi_b(a)) / d psi*_w =
+ * F_{b,w+a} psi_{-w-2a}, so with G_a = F_d^{(x)N} (Re chi_a / |chi_a|),
+ *     d m / d psi*_{y-a} += psi_{-y-a} G_a(y),   d mana / d psi* = (d m / d psi*) / (m ln 2),
+ * on the vector as given (not renormalised); undefined where some chi_b(a) = 0 (stabilizer
+ * states).  d = 3, 5, 7, 11, 13 with d^N <= 25600 (qutrits: N <= 9).  grad_dev: d^N amplitudes
+ * of the same dtype as psi on the device.  Per-CTA partials are summed in FP64 in a fixed
+ * order.  Synchronises `stream`.
+ */
+hadamag_status hadamag_mana_grad(hadamag_ctx_t ctx, const void* psi_dev, int N, int d,
+                                 hadamag_dtype dtype, double* mana_out, void* grad_dev,
+                                 hadamag_stream_t stream);
+
+/*
  * Mana of an N-qutrit density matrix, Sec. 3.3.3 (Algorithm 6; Eq. mana with
  * W_u = tr(rho A_u) / 3^N over the phase-space point operators A_u):
  *     mana = log2 sum_u |W_u|  (bits; 0 for stabilizer mixtures, equal to hadamag_mana on pure states).

@@ -113,13 +113,15 @@ def chi_fast(psi, d: int, chunk: int = 256) -> np.ndarray:
     return out
 
 
-def mana_grad(psi, d: int, chunk: int = 256):
+def mana_grad(psi, d: int, chunk: int = 256, small: float | None = None):
     """(mana, d mana / d psi*) on the unnormalised psi (Wirtinger gradient; mana =
     log2(sum_{a,b} |chi_b(a)| / d^N)).  From v_x = conj(psi_{x-a}) psi_{-x-a}:
         d chi_b(a) / d psi*_w = d conj(chi_b(a)) / d psi*_w = F_{b, w+a} psi_{-w-2a},
     so with y = w + a and G_a = F_d^{(x)N} (Re chi_a / |chi_a|) (F_d symmetric)
         d m / d psi*_{y-a} += psi_{-y-a} G_a(y),   d mana / d psi* = (d m / d psi*) / (m ln 2).
-    Defined where no chi_b(a) vanishes (not on stabilizer states)."""
+    Defined where no chi_b(a) vanishes (not on stabilizer states).  With `small` given, also
+    returns how many |chi_b(a)| are below it (entries whose sign a perturbation of that size
+    can flip, each moving d m / d psi* by at most 2 |psi|)."""
     _check_d(d)
     psi = np.asarray(psi, dtype=np.complex128)
     N = n_sites(psi.size, d)
@@ -127,13 +129,17 @@ def mana_grad(psi, d: int, chunk: int = 256):
     dig, pw = _digits(D, N, d), d ** np.arange(N)
     g = np.zeros(D, dtype=np.complex128)
     m = 0.0
+    below = 0
     for a0 in range(0, D, chunk):
         i1, i2 = _shift_indices(dig, dig[a0:a0 + chunk], d, pw)  # i1 = idx(y - a), i2 = idx(-y - a)
         chi = _transform_rows(np.conj(psi[i1]) * psi[i2], d, N)
         m += float(np.abs(chi).sum())
+        if small is not None:
+            below += int((np.abs(chi) < small).sum())
         G = _transform_rows(chi.real / np.abs(chi), d, N)
         np.add.at(g, i1.ravel(), (psi[i2] * G).ravel())
-    return float(np.log2(m / d ** N)), g / (m * np.log(2.0))
+    out = (float(np.log2(m / d ** N)), g / (m * np.log(2.0)))
+    return out + (below,) if small is not None else out
 
 
 def mana_fast(psi, d: int):

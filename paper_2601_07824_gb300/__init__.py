@@ -15,7 +15,8 @@ tensors into that ABI.
 from __future__ import annotations
 
 __all__ = ["sre", "sre_host", "sre_terms", "sre_even_sector", "mc_xstrings", "sre_mc", "sre_ti", "mana",
-           "mana_sums", "mana_qudit", "mana_mixed", "reduced_density_matrix", "sre_grad", "SREFunction",
+           "mana_sums", "mana_qudit", "mana_grad", "mana_mixed", "reduced_density_matrix", "sre_grad",
+           "SREFunction",
            "sre_batched",
            "context", "HadamagError", "PATH_AUTO", "PATH_CUDACORE", "PATH_TENSOR"]
 

@@ -186,6 +186,21 @@ def mana_qudit(psi: torch.Tensor, d: int):
     return m.value, list(sums)
 
 
+def mana_grad(psi: torch.Tensor, d: int = 3):
+    """(mana in bits, d mana / d psi*) of N qudits of odd prime dimension d (Wirtinger gradient
+    on the vector as given; a tensor like psi)."""
+    if int(d) < 2:
+        raise ValueError("d must be an odd prime")
+    N = _check_state(psi, int(d))
+    c = _ctx(psi)
+    m = ctypes.c_double()
+    grad = torch.empty_like(psi)
+    c.check(c.lib.hadamag_mana_grad(c.h, ctypes.c_void_p(psi.data_ptr()), N, int(d), _dtype_code(psi),
+                                    ctypes.byref(m), ctypes.c_void_p(grad.data_ptr()), _stream(psi)),
+            "hadamag_mana_grad")
+    return m.value, grad
+
+
 def mana_mixed(rho: torch.Tensor):
     """(mana in bits, [sum |chi|, sum chi, sum chi^2]) of an N-qutrit density matrix given as a
     3^N x 3^N CUDA tensor (Algorithm 6's W via the Algorithm 5 transform, Sec. 3.3.3)."""

@@ -30,10 +30,17 @@ cudaError_t launch_mana_onepass(const float2* src, int N, bool mixed, double* ou
 cudaError_t mana_twopass_grid(int N, bool mixed, int sm_count, int* grid);
 cudaError_t launch_mana_twopass(const ManaParams& P, bool mixed, int grid, cudaStream_t st);
 
-// Odd-prime qudits d = 5, 7, 11, 13 (qudit.cu): largest N with d^N <= 25600 (0 for other d),
-// and the launch writing grid <= max_grid per-CTA triples [sum |chi|, sum chi, sum chi^2].
+// Odd-prime qudits (qudit.cu): largest N with d^N <= 25600 for d = 3, 5, 7, 11, 13 (0 for other
+// d); the mana launch (d != 3) writing grid <= max_grid per-CTA triples [sum |chi|, sum chi,
+// sum chi^2]; the gradient launch, which also fills grid per-CTA partial gradients of d^N
+// double2 each (zeroed by the caller); and the finalize writing grad = (sum of partials) /
+// (msum[0] ln 2) as complex64 or complex128.
 int mana_qudit_max_n(int d);
 cudaError_t launch_mana_qudit(const float2* psi, int N, int d, double* out, int sm_count, int max_grid, int* grid,
                               cudaStream_t st);
+cudaError_t launch_mana_grad(const float2* psi, int N, int d, double* out, double2* gpart, int sm_count, int max_grid,
+                             int* grid, cudaStream_t st);
+cudaError_t launch_mana_grad_finalize(const double2* gpart, int parts, int dim, const double* msum, void* grad,
+                                      bool c128, cudaStream_t st);
 
 }  // namespace hm

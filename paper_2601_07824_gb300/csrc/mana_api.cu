@@ -143,6 +143,46 @@ extern "C" hadamag_status hadamag_mana_qudit(hadamag_ctx_t c, const void* psi, i
     return HADAMAG_OK;
 }
 
+extern "C" hadamag_status hadamag_mana_grad(hadamag_ctx_t c, const void* psi, int N, int d, hadamag_dtype dt,
+                                            double* mana_out, void* grad, hadamag_stream_t stream) {
+    if (!c) return HADAMAG_ERR_INVALID_ARG;
+    if (!aligned16(psi) || !aligned16(grad) || !mana_out) return fail(c, HADAMAG_ERR_INVALID_ARG, "null or misaligned pointer");
+    if (dt != HADAMAG_C64 && dt != HADAMAG_C128) return fail(c, HADAMAG_ERR_INVALID_ARG, "bad dtype");
+    const int nmax = mana_qudit_max_n(d);
+    if (nmax == 0) return fail(c, HADAMAG_ERR_UNSUPPORTED, "d must be 3, 5, 7, 11 or 13 (got %d)", d);
+    if (N < 1 || N > nmax) return fail(c, HADAMAG_ERR_INVALID_ARG, "N must be in [1, %d] for d = %d (got %d)", nmax, d, N);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    hadamag_status s;
+    cudaError_t e;
+    if ((s = begin(c, st))) return s;
+    int dim = 1;
+    for (int j = 0; j < N; ++j) dim *= d;
+    const float2* p;
+    if ((s = as_c64(c, psi, dim, dt, st, &p))) return s;
+    const int max_grid = c->sm_count * 2;
+    const size_t gbytes = (size_t)max_grid * dim * sizeof(double2);
+    if ((s = ensure_buf(c, c->part, (size_t)max_grid * 3 * sizeof(double)))) return s;
+    if ((s = ensure_buf(c, c->grad_acc, gbytes))) return s;
+    if ((e = cudaMemsetAsync(c->grad_acc.ptr, 0, gbytes, st)) != cudaSuccess) return cuda_fail(c, e, "memset");
+    int grid = 0;
+    e = launch_mana_grad(p, N, d, (double*)c->part.ptr, (double2*)c->grad_acc.ptr, c->sm_count, max_grid, &grid, st);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(c, e, "mana_grad");
+    e = launch_sum_triples((const double*)c->part.ptr, grid, (double*)c->res.ptr, st);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(c, e, "sum_triples");
+    e = launch_mana_grad_finalize((const double2*)c->grad_acc.ptr, grid, dim, (const double*)c->res.ptr, grad,
+                                  dt == HADAMAG_C128, st);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(c, e, "mana_grad_finalize");
+    if ((s = finish(c, (const double*)c->res.ptr, 3, st))) return s;
+    double m = std::log2(c->host_res[0] / (double)dim);
+    if (m == 0.0) m = 0.0;
+    *mana_out = m;
+    if (!std::isfinite(m)) return fail(c, HADAMAG_ERR_NONFINITE, "non-finite mana");
+    return HADAMAG_OK;
+}
+
 extern "C" hadamag_status hadamag_mana_mixed(hadamag_ctx_t c, const void* rho, int N, hadamag_dtype dt,
                                              double* mana_out, double* sums_out, hadamag_stream_t stream) {
     if (!c) return HADAMAG_ERR_INVALID_ARG;

@@ -87,3 +87,49 @@ def test_invalid_arguments():
         hm.mana_qudit(buf[:24].contiguous(), 5)
     # the context stays usable: |0...0> of 6 qudits has mana 0
     assert abs(hm.mana_qudit(buf[:5 ** 6].contiguous(), 5)[0]) <= stab_tol(5, 6)
+
+
+# ---- gradient of the mana ---------------------------------------------------------------
+# Mana is not differentiable where some chi_b(a) = 0: an entry within the FP32 error of zero
+# can take the other sign on the GPU, moving d m / d psi* by up to 2 |psi| (so d mana / d psi*
+# by 2 |psi| / (m ln 2)).  The tolerance is 1e-5 |g| plus that bound times the number K of
+# oracle entries below delta = 4 N d 2^-24 |psi|^2 (the FP32 error bound of a transformed
+# value).  The phase and scale identities hold for any sign pattern and stay strict.
+
+GRAD_CASES = [(3, 1), (3, 2), (3, 4), (3, 6), (3, 8), (5, 3), (7, 2), (7, 3), (11, 2), (13, 2)]
+
+
+@pytest.mark.parametrize("d,N", GRAD_CASES)
+def test_mana_gradient_vs_oracle(d, N):
+    psi = (I.gaussian_state(N, 3000 * d + N, d=d) * 1.2).astype(np.complex64)
+    m, g = hm.mana_grad(on_dev(psi), d)
+    g = g.cpu().numpy().astype(np.complex128)
+    p = psi.astype(np.complex128)
+    delta = 4 * N * d * 2.0 ** -24 * float(np.vdot(p, p).real)
+    mo, go, K = Q.mana_grad(p, d, small=delta)
+    assert abs(m - mo) <= 1e-6 * max(1.0, abs(mo))
+    msum = d ** N * 2.0 ** mo
+    tol = 1e-5 * np.linalg.norm(go) + 2 * np.linalg.norm(p) * K / (msum * math.log(2.0))
+    assert np.linalg.norm(g - go) <= tol, (d, N, K, np.linalg.norm(g - go) / np.linalg.norm(go))
+
+
+@pytest.mark.parametrize("d,N,dtype", [(3, 9, np.complex64), (5, 4, np.complex128), (13, 3, np.complex64)])
+def test_mana_gradient_identities(d, N, dtype):
+    psi = (I.gaussian_state(N, 3100 * d + N, d=d) * 0.8).astype(dtype)
+    m, g = hm.mana_grad(on_dev(psi), d)
+    assert g.dtype == on_dev(psi).dtype
+    g = g.cpu().numpy().astype(np.complex128)
+    p = psi.astype(np.complex128)
+    # phase invariance and mana(c psi) = mana(psi) + 2 log2 c
+    assert abs(np.imag(np.vdot(g, p))) <= 1e-5 * np.linalg.norm(g) * np.linalg.norm(p)
+    assert 2 * np.real(np.vdot(g, p)) == pytest.approx(2 / math.log(2.0), rel=1e-5)
+    assert abs(m - hm.mana_qudit(on_dev(psi), d)[0]) <= 1e-6 * max(1.0, abs(m))
+
+
+def test_mana_gradient_invalid_arguments():
+    buf = torch.zeros(3 ** 10, dtype=torch.complex64, device=DEV)
+    with pytest.raises(hm.HadamagError) as e:
+        hm.mana_grad(buf, 3)  # 3^10 > 25600
+    assert e.value.code == 1
+    with pytest.raises(ValueError):
+        hm.mana_grad(buf[:10].contiguous(), 3)

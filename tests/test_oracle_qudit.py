@@ -113,3 +113,12 @@ def test_mana_gradient_phase_and_scale_identities(d, N):
     assert abs(np.imag(np.vdot(g, psi))) < 1e-12
     # mana(c psi) = mana(psi) + 2 log2 c: 2 Re sum conj(g) psi = 2 / ln 2
     assert 2 * np.real(np.vdot(g, psi)) == pytest.approx(2 / np.log(2.0), rel=1e-12)
+
+
+def test_mana_gradient_counts_small_entries():
+    psi = I.gaussian_state(2, 97, d=5)
+    m, g = Q.mana_grad(psi, 5)
+    m0, g0, k0 = Q.mana_grad(psi, 5, small=0.0)
+    _, _, kall = Q.mana_grad(psi, 5, small=1e9)
+    assert k0 == 0 and kall == 5 ** 4
+    assert m0 == m and np.array_equal(g0, g)
