@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--extra", action="store_true",
                     help="also time N=22, mana N=11, MC N=28, batched, thermodynamic integration N=20, "
-                         "mixed-state mana N=8")
+                         "mixed-state mana N=8, even-sector SRE N=20, qudit mana d=5, mana gradient")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--xstrings", type=int, default=0,
                     help="profiling aid: each step evaluates only the first K X-strings of the "
@@ -462,6 +462,28 @@ def extra_workloads(hm, dev, sm_count):
         return {"points_per_s": pts / dt, "s": dt, "mana": r[0], "rho_read_GBps": pts * 8 / dt / 1e9,
                 "rdm_s": t_rdm, "rdm_tflops": 8.0 * 9.0 ** 8 * 3.0 ** 2 / t_rdm / 1e12}
     guard("mana_mixed_N8_of_10", mixed8)
+
+    # even-weight X-sectors only (U(1) state at half filling, N = 20): half the work of the full sum
+    def even20():
+        psi = torch.from_numpy(inputs.u1_state(20, 10, 2003, dtype=np.complex64)).to(dev)
+        t_full, rf = timed(lambda: hm.sre(psi, 2.0))
+        t_even, re_ = timed(lambda: hm.sre_even_sector(psi, 2.0))
+        return {"full_s": t_full, "even_s": t_even, "speedup": t_full / t_even, "M2_full": rf[0], "M2_even": re_[0],
+                "even_strings_per_s": 2.0 ** 39 / t_even}
+    guard("sre_even_sector_N20_u1", even20)
+
+    # odd-prime qudits: mana at d = 5, N = 6, and the qutrit mana gradient at N = 9
+    def qudit5():
+        psi = torch.from_numpy(inputs.gaussian_state(6, 501, d=5, dtype=np.complex64)).to(dev)
+        dt, r = timed(lambda: hm.mana_qudit(psi, 5), reps=3)
+        return {"points_per_s": 25.0 ** 6 / dt, "s": dt, "mana": r[0]}
+    guard("mana_qudit_d5_N6", qudit5)
+
+    def grad3():
+        psi = torch.from_numpy(inputs.gaussian_state(9, 901, d=3, dtype=np.complex64)).to(dev)
+        dt, r = timed(lambda: hm.mana_grad(psi, 3), reps=3)
+        return {"points_per_s": 9.0 ** 9 / dt, "s": dt, "mana": r[0]}
+    guard("mana_grad_d3_N9", grad3)
     return out
 
 
