@@ -1,282 +1,9 @@
-// sre_fwd.cu -- exact SRE forward kernels (paper Sec. 3.1.2, Algorithm 2; Eq. sre).
-//
-// For every X-string a the kernels form the half-length pair product w_a (see common.cuh),
-// apply the unnormalised Walsh-Hadamard transform over its N-1 index bits and reduce
-// sum_b |c_a(b)|^{2n}, sum_b |c_a(b)|^2 (lost_norm, Sec. 4.1) and, for n = 1,
-// sum_b |c|^2 log2 |c|^2.  Two shapes:
-//
-//   * sre_onepass<L>   (N <= 15, L = N-1 <= 14): a group of 2^(L-5) threads owns one X-string,
-//     32 complex values per thread, shared-memory exchanges between 5-bit register rounds.
-//   * sre_twopass<M>   (N = 16..24, L = 10 + M): a persistent kernel over a static task list.
-//     Pass 1 (one warp per (a, unit)): pair product + transform over the 10 low bits of z',
-//     written to a scratch slot in L2.  Pass 2 (one CTA per (a, column tile)): transform over
-//     the M high bits + reduction.  Pass-2 tasks of a batch wait (bounded) on a counter of
-//     finished pass-1 tasks; pass-1 tasks reusing a slot wait for that slot's pass-2 tasks.
-//     Tasks are taken round-robin in a fixed global order in which every task only waits on
-//     earlier tasks, so a co-resident grid cannot deadlock, and the FP64 sums are deterministic.
-#include "common.cuh"
-#include "pairs.cuh"
-#include "sre_fwd.h"
+// sre_fwd.cu -- host dispatch of the exact-SRE forward kernels (paper Sec. 3.1.2, Algorithm 2)
+// and the small reduction / conversion kernels they share.  The kernels themselves are in
+// sre_fwd_kernels.cuh, instantiated one accumulation mode per translation unit (sre_fwd_n*.cu).
+#include "sre_fwd_kernels.cuh"
 
 namespace hm {
-
-// ------------------------------------------------------------------------------------------
-// One-pass kernel.
-template <int L, int MODE>
-__global__ void __launch_bounds__(OnepassShape<L>::NT)
-sre_onepass(const float2* __restrict__ psi, int N, double nq, int64_t count,
-            const int64_t* __restrict__ a_list, double* __restrict__ out, int per_a, int* status) {
-    using Sh = OnepassShape<L>;
-    constexpr int E = Sh::E, G = Sh::G, GPC = Sh::GPC;
-    using S = TileSched<L, 0, E>;
-    extern __shared__ float2 smem[];
-    __shared__ float red[16][4];
-    __shared__ double redd[16];
-    const uint32_t tid = threadIdx.x, gi = tid / G, t = tid % G;
-    float2* sm = smem + (size_t)gi * (L >= 5 ? tile_slots(L) : (1u << L));
-    const int64_t ngroups = (int64_t)gridDim.x * GPC;
-    const int64_t gg = (int64_t)blockIdx.x * GPC + gi;
-    const int64_t iters = (count + ngroups - 1) / ngroups;
-    const int64_t dim = int64_t(1) << N;
-    double acc[3] = {0.0, 0.0, 0.0};
-
-    for (int64_t it = 0; it < iters; ++it) {
-        const int64_t idx = gg + it * ngroups;
-        bool valid = idx < count;
-        int64_t a = valid ? (a_list ? a_list[idx] : idx) : 0;
-        if (a < 0 || a >= dim) {
-            if (valid) atomicOr(status, ST_BADARG);
-            valid = false;
-            a = 0;
-        }
-        const int p = a ? msb64(a) : 0;
-        float2 x[1 << E];
-#pragma unroll
-        for (int i = 0; i < (1 << E); ++i) x[i] = pair_product(psi, deposit<E>(t, i, S::S0), a, p);
-        reg_fwht<E, 0, E>(x);
-        if constexpr (G <= 32) tile_rounds<L, 0, E, 1>(x, sm, t, SyncWarp());
-        else tile_rounds<L, 0, E, 1>(x, sm, t, SyncCta());
-
-        Acc<MODE> ac;
-#pragma unroll
-        for (int i = 0; i < (1 << E); ++i) ac.add(x[i], nq);
-        ac.fold();
-        float q = ac.q, s1 = ac.s1, u = ac.u;
-        double qd = ac.qd;
-        double v[3];
-        if constexpr (G <= 32) {
-            warp_sum3<MODE>(q, s1, u, qd, G);
-        } else {
-            warp_sum3<MODE>(q, s1, u, qd, 32);
-            if ((tid & 31) == 0) {
-                red[tid >> 5][0] = q; red[tid >> 5][1] = s1; red[tid >> 5][2] = u;
-                redd[tid >> 5] = qd;
-            }
-            __syncthreads();
-            if (tid == 0) {
-                float a0 = 0.f, a1 = 0.f, a2 = 0.f;
-                double ad = 0.0;
-                for (int w = 0; w < (G >> 5); ++w) { a0 += red[w][0]; a1 += red[w][1]; a2 += red[w][2]; ad += redd[w]; }
-                q = a0; s1 = a1; u = a2; qd = ad;
-            }
-            __syncthreads();
-        }
-        if (t == 0 && valid) {
-            finish3<MODE>(q, s1, u, qd, nq, v);
-            if (per_a) {
-                out[idx * 3 + 0] = v[0]; out[idx * 3 + 1] = v[1]; out[idx * 3 + 2] = v[2];
-            } else {
-                acc[0] += v[0]; acc[1] += v[1]; acc[2] += v[2];
-            }
-        }
-    }
-    if (!per_a) {
-        // fixed-order combination of the group leaders' FP64 sums
-        __syncthreads();
-        double* dd = reinterpret_cast<double*>(smem);
-        if (t == 0) { dd[gi * 3 + 0] = acc[0]; dd[gi * 3 + 1] = acc[1]; dd[gi * 3 + 2] = acc[2]; }
-        __syncthreads();
-        if (tid == 0) {
-            double s0 = 0.0, s1d = 0.0, s2 = 0.0;
-            for (int g = 0; g < GPC; ++g) { s0 += dd[g * 3]; s1d += dd[g * 3 + 1]; s2 += dd[g * 3 + 2]; }
-            out[blockIdx.x * 3 + 0] = s0; out[blockIdx.x * 3 + 1] = s1d; out[blockIdx.x * 3 + 2] = s2;
-        }
-    }
-}
-
-// ------------------------------------------------------------------------------------------
-// Persistent two-pass kernel, 256 threads per CTA (two CTAs per SM).
-//   K1 = 10: pass 1 is warp-level (each warp one (X-string, unit) of 2^10 values);
-//   K1 = 13: pass 1 is CTA-level (the CTA does one (X-string, unit) of 2^13 values).
-//   The scratch of one X-string is [2^M units][2^K1 columns]; a pass-2 tile is all 2^M units
-//   x 2^(13-M) consecutive columns (2^13 values).
-template <int K1, int M, int MODE>
-__global__ void __launch_bounds__(256, 2) sre_twopass(TwoPassParams P) {
-    using Sh = TwoPassShape<K1, M>;
-    constexpr int L = Sh::L, LOGT = Sh::LOGT, T = Sh::T, TILES = Sh::TILES;
-    extern __shared__ float2 smem[];
-    __shared__ float red[8][4];
-    __shared__ double redd[8];
-    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const float2* __restrict__ psi = P.psi;
-    const int64_t dim = int64_t(1) << P.N;
-    const int64_t per_stage = (int64_t)P.p1 + P.p2;
-    const int64_t total = P.n_batches * per_stage;
-    double acc[3] = {0.0, 0.0, 0.0};
-
-    // (stage, kind, index) of a task: stage s runs pass 1 of batch s, then pass 2 of batch s-1.
-    auto decode = [&](int64_t task, int64_t& g, int& kind, int& r) {
-        if (task < P.p1) { g = 0; kind = 1; r = (int)task; return; }
-        const int64_t tt = task - P.p1;
-        const int64_t s = 1 + tt / per_stage;
-        const int rr = (int)(tt % per_stage);
-        if (s < P.n_batches && rr < P.p1) { g = s; kind = 1; r = rr; }
-        else { g = s - 1; kind = 2; r = (s < P.n_batches) ? rr - P.p1 : rr; }
-    };
-    // counter and target a task waits on (none for pass 1 of the first R batches)
-    auto dependency = [&](int64_t g, int kind, const unsigned*& ctr, unsigned& need) {
-        const int slot = (int)(g % P.R);
-        if (kind == 1) {
-            ctr = (g >= P.R) ? P.done2 + slot : nullptr;
-            need = (unsigned)((g / P.R) * P.p2) + P.wait_bias;
-        } else {
-            ctr = P.done1 + slot;
-            need = (unsigned)((g / P.R + 1) * P.p1) + P.wait_bias;
-        }
-    };
-
-    unsigned seen = 0;  // thread 0: relaxed read of the next task's counter, one task ahead
-    {
-        int64_t g; int kind, r;
-        const unsigned* c; unsigned need;
-        if (tid == 0 && (int64_t)blockIdx.x < total) {
-            decode(blockIdx.x, g, kind, r);
-            dependency(g, kind, c, need);
-            if (c) seen = ld_relaxed(c);
-        }
-    }
-
-    for (int64_t task = blockIdx.x; task < total; task += gridDim.x) {
-        int64_t g;
-        int kind, r;
-        decode(task, g, kind, r);
-        const int slot = (int)(g % P.R);
-        float2* sbase = P.scratch + (size_t)slot * P.A * ((size_t)1 << L);
-        {
-            const unsigned* c;
-            unsigned need;
-            dependency(g, kind, c, need);
-            if (c && !cta_wait_geq(c, need, P.status, P.spin_limit, seen)) return;
-        }
-        if (tid == 0 && task + gridDim.x < total) {  // prefetch the next task's counter
-            int64_t g2; int k2, r2;
-            const unsigned* c2; unsigned n2;
-            decode(task + gridDim.x, g2, k2, r2);
-            dependency(g2, k2, c2, n2);
-            seen = c2 ? ld_relaxed(c2) : 0u;
-        }
-
-        if (kind == 1) {
-            // ---- pass 1: pair product + transform over the K1 low bits of z' ----------------
-            int a_idx, sub;
-            int64_t unit;
-            if constexpr (K1 == 10) { a_idx = warp % P.A; unit = ((int64_t)r * P.U + warp / P.A) * 2; sub = warp; }
-            else { a_idx = 0; unit = r; sub = 0; }
-            const int64_t i = g * P.A + a_idx;
-            bool valid = i < P.count;
-            int64_t a = valid ? (P.a_list ? P.a_list[i] : i) : 0;
-            if (a < 0 || a >= dim) {
-                if (valid && (tid & (K1 == 10 ? 31 : 255)) == 0) atomicOr(P.status, ST_BADARG);
-                valid = false;
-            }
-            if (valid) {
-                float2 x[32];
-                if constexpr (K1 == 10) {
-                    float2* sm = smem + sub * tile_slots(10);
-                    for (int uu = 0; uu < 2; ++uu) {  // two consecutive units per warp
-                        const PairRows<K1, M> pr(a, unit + uu);
-                        float2* dst = sbase + (size_t)a_idx * ((size_t)1 << L) + ((size_t)(unit + uu) << K1);
-#pragma unroll
-                        for (int k = 0; k < 32; ++k) x[k] = pr.value(psi, a, lane | (k << 5));
-                        reg_fwht<5, 0, 5>(x);
-                        tile_rounds<10, 0, 5, 1>(x, sm, lane, SyncWarp());
-                        // registers hold j bits [0,5), lanes bits [5,10): store column (k<<5)|lane
-#pragma unroll
-                        for (int k = 0; k < 32; ++k) __stcg(dst + lane + (k << 5), x[k]);
-                    }
-                } else {
-                    const PairRows<K1, M> pr(a, unit);
-                    float2* dst = sbase + (size_t)a_idx * ((size_t)1 << L) + ((size_t)unit << K1);
-#pragma unroll
-                    for (int k = 0; k < 32; ++k) x[k] = pr.value(psi, a, deposit<5>(tid, k, 8));
-                    reg_fwht<5, 0, 5>(x);
-                    tile_rounds<13, 0, 5, 1>(x, smem, tid, SyncCta());
-                    constexpr int SL = TileSched<13, 0, 5>::last_shift();
-#pragma unroll
-                    for (int k = 0; k < 32; ++k) __stcg(dst + deposit<5>(tid, k, SL), x[k]);
-                }
-            }
-            __syncthreads();
-            if (tid == 0) {
-                __threadfence();
-                red_release_add(P.done1 + slot, 1u);
-            }
-        } else {
-            // ---- pass 2: transform over the M high bits of z' + reduction ------------------
-            const int a_idx = r / (TILES / 2);
-            const int64_t i = g * P.A + a_idx;
-            if (i < P.count) for (int tile = (r % (TILES / 2)) * 2, te = tile + 2; tile < te; ++tile) {
-                const float2* src = sbase + (size_t)a_idx * ((size_t)1 << L) + (size_t)tile * T;
-                float2 x[32];
-#pragma unroll
-                for (int k = 0; k < 32; ++k) {
-                    const uint32_t j = deposit<5>(tid, k, 8);  // tile index (row << LOGT) | col
-                    x[k] = __ldcg(src + ((size_t)(j >> LOGT) << K1) + (j & (T - 1)));
-                }
-                reg_fwht<5, 0, 5>(x);
-                tile_rounds<13, LOGT, 5, 1>(x, smem, tid, SyncCta());
-                if constexpr (Sh::DISCARD) {
-                    // every value of the tile is in registers: drop its lines from L2 unwritten
-                    if constexpr (TileSched<13, LOGT, 5>::NR == 1) __syncthreads();
-                    constexpr int LPR = (T * 8) / 128;  // 128-byte lines per tile row
-#pragma unroll
-                    for (int q = tid; q < (1 << M) * LPR; q += 256)
-                        discard_l2_line(src + ((size_t)(q / LPR) << K1) + (q % LPR) * 16);
-                }
-                Acc<MODE> ac;
-#pragma unroll
-                for (int k = 0; k < 32; ++k) ac.add(x[k], P.nq);
-                ac.fold();
-                float q = ac.q, s1 = ac.s1, u = ac.u;
-                double qd = ac.qd;
-                warp_sum3<MODE>(q, s1, u, qd, 32);
-                if (lane == 0) { red[warp][0] = q; red[warp][1] = s1; red[warp][2] = u; redd[warp] = qd; }
-                __syncthreads();
-                if (tid == 0) {
-                    double v[3], tot[3] = {0.0, 0.0, 0.0};
-                    for (int w = 0; w < 8; ++w) {
-                        finish3<MODE>(red[w][0], red[w][1], red[w][2], redd[w], P.nq, v);
-                        tot[0] += v[0]; tot[1] += v[1]; tot[2] += v[2];
-                    }
-                    if (P.per_a) {
-                        double* o = P.out + ((size_t)i * TILES + tile) * 3;
-                        o[0] = tot[0]; o[1] = tot[1]; o[2] = tot[2];
-                    } else {
-                        acc[0] += tot[0]; acc[1] += tot[1]; acc[2] += tot[2];
-                    }
-                }
-                __syncthreads();  // red[] is reused by the next tile
-            }
-            __syncthreads();
-            if (tid == 0) red_release_add(P.done2 + slot, 1u);
-        }
-    }
-    if (!P.per_a && tid == 0) {
-        P.out[blockIdx.x * 3 + 0] = acc[0];
-        P.out[blockIdx.x * 3 + 1] = acc[1];
-        P.out[blockIdx.x * 3 + 2] = acc[2];
-    }
-}
 
 // ------------------------------------------------------------------------------------------
 // Deterministic FP64 reduction of `n` triples (fixed per-thread strides, fixed tree).
@@ -319,47 +46,14 @@ __global__ void c128_to_c64(const double2* __restrict__ in, float2* __restrict__
 }
 
 // ------------------------------------------------------------------------------------------
-// Host launchers.
-
-template <int L, int MODE>
-static cudaError_t launch_onepass_t(OnepassArgs& A, int sm_count, cudaStream_t st) {
-    using Sh = OnepassShape<L>;
-    size_t smem = (size_t)Sh::GPC * (L >= 5 ? tile_slots(L) : (1u << L)) * sizeof(float2);
-    const size_t comb = (size_t)Sh::GPC * 3 * sizeof(double);
-    if (smem < comb) smem = comb;
-    auto k = sre_onepass<L, MODE>;
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    int occ = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, Sh::NT, smem);
-    if (e != cudaSuccess) return e;
-    if (occ < 1) occ = 1;
-    int64_t need = (A.count + Sh::GPC - 1) / Sh::GPC;
-    int64_t cap = (int64_t)occ * sm_count;
-    if (A.grid > 0 && A.grid < cap) cap = A.grid;
-    A.grid = (int)(need < cap ? need : cap);
-    if (A.grid < 1) A.grid = 1;
-    k<<<A.grid, Sh::NT, smem, st>>>(A.psi, A.N, A.nq, A.count, A.a_list, A.out, A.per_a, A.status);
-    return cudaGetLastError();
-}
-
-template <int MODE>
-static cudaError_t launch_onepass_m(OnepassArgs& A, int sm_count, cudaStream_t st) {
-    switch (A.N - 1) {
-#define HM_CASE(LL) case LL: return launch_onepass_t<LL, MODE>(A, sm_count, st);
-        HM_CASE(0) HM_CASE(1) HM_CASE(2) HM_CASE(3) HM_CASE(4) HM_CASE(5) HM_CASE(6) HM_CASE(7)
-        HM_CASE(8) HM_CASE(9) HM_CASE(10) HM_CASE(11) HM_CASE(12) HM_CASE(13) HM_CASE(14)
-#undef HM_CASE
-        default: return cudaErrorInvalidValue;
-    }
-}
+// Host dispatch on the accumulation mode.
 
 cudaError_t launch_onepass(OnepassArgs& A, int mode, int sm_count, cudaStream_t st) {
     switch (mode) {
-        case 0: return launch_onepass_m<0>(A, sm_count, st);
-        case 1: return launch_onepass_m<1>(A, sm_count, st);
-        case 2: return launch_onepass_m<2>(A, sm_count, st);
-        case 3: return launch_onepass_m<3>(A, sm_count, st);
+        case 0: return sre_fwd_onepass_n0(A, sm_count, st);
+        case 1: return sre_fwd_onepass_n1(A, sm_count, st);
+        case 2: return sre_fwd_onepass_n2(A, sm_count, st);
+        case 3: return sre_fwd_onepass_n3(A, sm_count, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -368,66 +62,16 @@ cudaError_t launch_onepass(OnepassArgs& A, int mode, int sm_count, cudaStream_t 
 // pass-2 tiles keep rows of >= 16 values whenever possible.
 int twopass_k1(int N) { return N <= 20 ? 10 : 13; }
 
-template <int K1, int M>
-static constexpr size_t twopass_smem() {
-    return (K1 == 10 ? 8 * tile_slots(10) : tile_slots(13)) * sizeof(float2) > tile_slots(13) * sizeof(float2)
-               ? 8 * tile_slots(10) * sizeof(float2)
-               : tile_slots(13) * sizeof(float2);
-}
-
-template <int K1, int M, int MODE>
-static cudaError_t twopass_prepare(int* occ) {
-    auto k = sre_twopass<K1, M, MODE>;
-    constexpr size_t smem = twopass_smem<K1, M>();
-    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, 256, smem);
-}
-
-template <int K1, int M, int MODE>
-static cudaError_t launch_twopass_t(const TwoPassParams& P, int grid, cudaStream_t st) {
-    int occ = 0;
-    cudaError_t e = twopass_prepare<K1, M, MODE>(&occ);
-    if (e != cudaSuccess) return e;
-    sre_twopass<K1, M, MODE><<<grid, 256, twopass_smem<K1, M>(), st>>>(P);
-    return cudaGetLastError();
-}
-
-// N -> (K1, M): N = 16..20 -> (10, N-11); N = 21..24 -> (13, N-14).
-#define HM_TWOPASS_SWITCH(N_, EXPR)                                              \
-    switch (N_) {                                                                \
-        case 16: { constexpr int KK = 10, MM = 5; EXPR; }                        \
-        case 17: { constexpr int KK = 10, MM = 6; EXPR; }                        \
-        case 18: { constexpr int KK = 10, MM = 7; EXPR; }                        \
-        case 19: { constexpr int KK = 10, MM = 8; EXPR; }                        \
-        case 20: { constexpr int KK = 10, MM = 9; EXPR; }                        \
-        case 21: { constexpr int KK = 13, MM = 7; EXPR; }                        \
-        case 22: { constexpr int KK = 13, MM = 8; EXPR; }                        \
-        case 23: { constexpr int KK = 13, MM = 9; EXPR; }                        \
-        case 24: { constexpr int KK = 13, MM = 10; EXPR; }                       \
-        default: return cudaErrorInvalidValue;                                   \
-    }
-
-template <int MODE>
-static cudaError_t launch_twopass_m(const TwoPassParams& P, int grid, cudaStream_t st) {
-    HM_TWOPASS_SWITCH(P.N, return (launch_twopass_t<KK, MM, MODE>(P, grid, st)))
-}
-
-template <int MODE>
-static cudaError_t twopass_occ_m(int N, int* occ) {
-    HM_TWOPASS_SWITCH(N, return (twopass_prepare<KK, MM, MODE>(occ)))
-}
-
 int twopass_tiles_per_a(int N) {
     HM_TWOPASS_SWITCH(N, return (TwoPassShape<KK, MM>::TILES))
 }
 
 cudaError_t launch_twopass(const TwoPassParams& P, int mode, int grid, cudaStream_t st) {
     switch (mode) {
-        case 0: return launch_twopass_m<0>(P, grid, st);
-        case 1: return launch_twopass_m<1>(P, grid, st);
-        case 2: return launch_twopass_m<2>(P, grid, st);
-        case 3: return launch_twopass_m<3>(P, grid, st);
+        case 0: return sre_fwd_twopass_n0(P, grid, st);
+        case 1: return sre_fwd_twopass_n1(P, grid, st);
+        case 2: return sre_fwd_twopass_n2(P, grid, st);
+        case 3: return sre_fwd_twopass_n3(P, grid, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -436,10 +80,10 @@ cudaError_t twopass_max_grid(int N, int mode, int sm_count, int* grid) {
     int occ = 0;
     cudaError_t e;
     switch (mode) {
-        case 0: e = twopass_occ_m<0>(N, &occ); break;
-        case 1: e = twopass_occ_m<1>(N, &occ); break;
-        case 2: e = twopass_occ_m<2>(N, &occ); break;
-        case 3: e = twopass_occ_m<3>(N, &occ); break;
+        case 0: e = sre_fwd_twopass_occ_n0(N, &occ); break;
+        case 1: e = sre_fwd_twopass_occ_n1(N, &occ); break;
+        case 2: e = sre_fwd_twopass_occ_n2(N, &occ); break;
+        case 3: e = sre_fwd_twopass_occ_n3(N, &occ); break;
         default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;
