@@ -27,6 +27,14 @@ Readings (the printed text is inconsistent here):
     bits drawn from the step's first output r as b1 = r mod N, b2 = (r div N) mod (N-1),
     b2 += 1 if b2 >= b1 (a symmetric move that spans the sector).  Then Z_0 = 2^(N-1),
     Z_1 = S_2 + 2^(N-1) eps and M_2 = 1 - log2(exp(-I) - eps).
+  * Statistical error (Eqs. Var_I_eps, m2error): Var[I] ~ sum_l w_l^2 2 tau_int sigma_f^2 / n_l,
+    delta M_2 = (d M_2 / d I) sqrt(Var[I]).  The paper does not say how 2 tau_int sigma_f^2 / n_l
+    is estimated; here by non-overlapping batch means (the variance of the mean of a correlated
+    series is the spread of means of batches much longer than tau_int): the n_s recorded
+    samples of a chain are cut into B = min(32, n_s) batches of K = n_s div B consecutive
+    samples (the last n_s - B K samples enter the mean only), and
+    Var_l = sum_b (m_b - mbar)^2 / (B (B - 1)).  d M_2 / d I = exp(-I) / ((exp(-I) - eps) ln 2).
+    With B < 2 the error is reported as 0.
 """
 from __future__ import annotations
 
@@ -140,6 +148,11 @@ def energies_sector(psi, eps: float, sector: str) -> np.ndarray:
     return -np.log(S)
 
 
+def n_batches(n_s: int) -> int:
+    """Batches of the batch-means error estimate: B = min(32, n_s)."""
+    return min(32, n_s)
+
+
 def metropolis_means(f, N: int, L: int, n_s: int, seed: int, burn_in: int = 0, record: dict | None = None,
                      sector: str | None = None):
     """Algorithm 3's chains: per beta_l, n_s Metropolis steps (one-bit flips, acceptance
@@ -149,16 +162,21 @@ def metropolis_means(f, N: int, L: int, n_s: int, seed: int, burn_in: int = 0, r
     f is the energy table (f[a] for every a) or a callable a -> f(a).  With `record` given,
     record["traj"][l, t] is the chain state after step t (burn-in included) and
     record["margin"][l, t] = |u - p_acc| of that step's decision (how far the decision was
-    from going the other way).  sector="even" keeps the chains on even-weight X-strings."""
+    from going the other way), and record["batch_sums"][l, b] the sum of the recorded energies
+    of batch b (batches of n_s div B consecutive recorded steps, B = n_batches(n_s)).
+    sector="even" keeps the chains on even-weight X-strings."""
     import oracle
     energy = f if callable(f) else f.__getitem__
     betas = np.linspace(0.0, 1.0, L)
     means = np.zeros(L)
     visits = np.zeros((L, 1 << N), dtype=np.int64) if not callable(f) else None
     steps = burn_in + n_s
+    B = n_batches(n_s)
+    K = n_s // B
     if record is not None:
         record["traj"] = np.zeros((L, steps), dtype=np.int64)
         record["margin"] = np.zeros((L, steps))
+        record["batch_sums"] = np.zeros((L, B))
     for l, beta in enumerate(betas):
         r = oracle.splitmix64(seed + l, 1 + 2 * steps)
         a = int(r[0] >> np.uint64(64 - N)) if N > 0 else 0
@@ -187,8 +205,26 @@ def metropolis_means(f, N: int, L: int, n_s: int, seed: int, burn_in: int = 0, r
                 acc += fa
                 if visits is not None:
                     visits[l, a] += 1
+                b = (t - burn_in) // K
+                if record is not None and b < B:
+                    record["batch_sums"][l, b] += fa
         means[l] = acc / n_s
     return means, visits
+
+
+def m2_stderr(batch_sums: np.ndarray, n_s: int, I: float, eps: float = 0.0) -> float:
+    """delta M_2 of Eq. m2error from the chains' batch sums (batch-means reading above)."""
+    L, B = batch_sums.shape
+    if B < 2:
+        return 0.0
+    K = n_s // B
+    w = simpson_weights(L)
+    var_I = 0.0
+    for l in range(L):
+        m = batch_sums[l] / K
+        var_I += w[l] ** 2 * float(np.sum((m - m.mean()) ** 2)) / (B * (B - 1))
+    slope = math.exp(-I) / ((math.exp(-I) - eps) * math.log(2.0))
+    return slope * math.sqrt(var_I)
 
 
 def m2_metropolis(psi, L: int, n_s: int, seed: int, burn_in: int = 0, eps: float = 0.0,

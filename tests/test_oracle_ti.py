@@ -223,3 +223,51 @@ def test_even_sector_planted_mistakes_fail():
     rec = {}
     ti.metropolis_means(ti.energies(psi, 1e-3), 7, 3, 50, seed=3, record=rec)
     assert any(bin(int(a)).count("1") % 2 for a in rec["traj"].ravel())
+
+
+# ---- statistical error (Eqs. Var_I_eps, m2error; batch-means reading) ----------------------
+
+def test_batch_sums_partition_the_recorded_energies():
+    psi = I.gaussian_state(6, 41)
+    f = ti.energies(psi)
+    for n_s in (1, 7, 32, 100, 1000):
+        rec = {}
+        means, _ = ti.metropolis_means(f, 6, 3, n_s, seed=5, burn_in=3, record=rec)
+        B = ti.n_batches(n_s)
+        K = n_s // B
+        assert rec["batch_sums"].shape == (3, B)
+        for l in range(3):
+            fr = f[rec["traj"][l, 3:]]
+            np.testing.assert_allclose(rec["batch_sums"][l], fr[:B * K].reshape(B, K).sum(1), rtol=1e-13)
+            assert means[l] == pytest.approx(fr.mean(), rel=1e-13)
+    assert ti.m2_stderr(np.ones((3, 1)), 1, 1.0) == 0.0
+
+
+def test_reported_error_matches_the_spread_over_seeds():
+    # the batch-means error must describe the actual scatter of independent estimates
+    psi = I.gaussian_state(6, 42)
+    L, n_s, burn = 5, 3000, 200
+    f = ti.energies(psi)
+    est, errs = [], []
+    for seed in range(40):
+        rec = {}
+        means, _ = ti.metropolis_means(f, 6, L, n_s, seed=1000 * seed, burn_in=burn, record=rec)
+        I_ = float(np.dot(ti.simpson_weights(L), means))
+        est.append(ti.m2_from_integral(I_))
+        errs.append(ti.m2_stderr(rec["batch_sums"], n_s, I_))
+    spread, typical = float(np.std(est, ddof=1)), float(np.median(errs))
+    assert 0.6 < spread / typical < 1.6, (spread, typical)
+    # and the estimates scatter around the exact M_2 accordingly
+    M2 = oracle.sre(psi, 2.0)[0]
+    assert abs(np.mean(est) - M2) < 4 * spread / np.sqrt(len(est)) + 2e-3
+
+
+def test_error_slope_with_eps():
+    # M_2 = -log2(exp(-I) - eps): d M_2 / d I = exp(-I) / ((exp(-I) - eps) ln 2)
+    bs = np.array([[1.0, 2.0, 3.0, 5.0], [2.0, 2.0, 4.0, 1.0], [0.0, 1.0, 0.0, 2.0]])
+    e0 = ti.m2_stderr(bs, 8, 0.7)
+    e1 = ti.m2_stderr(bs, 8, 0.7, eps=0.1)
+    assert e1 / e0 == pytest.approx(np.exp(-0.7) / (np.exp(-0.7) - 0.1), rel=1e-12)
+    h = 1e-6
+    slope = (ti.m2_from_integral(0.7 + h, 0.1) - ti.m2_from_integral(0.7 - h, 0.1)) / (2 * h)
+    assert e1 / e0 == pytest.approx(slope * np.log(2.0), rel=1e-6)
