@@ -447,7 +447,8 @@ def extra_workloads(hm, dev, sm_count):
         dt, r = timed(lambda: hm.sre_ti(psi, L, n_s, 2002, burn_in=burn), warm=False)
         evals = L * (n_s + burn + 1)
         return {"strings_per_s": evals * 2.0 ** 20 / dt, "evaluations_per_s": evals / dt,
-                "steps_per_s": (n_s + burn) / dt, "s": dt, "M2": r[0], "L": L, "n_s": n_s, "burn_in": burn}
+                "steps_per_s": (n_s + burn) / dt, "s": dt, "M2": r[0], "dM2": r[1], "L": L, "n_s": n_s,
+                "burn_in": burn}
     guard("ti_N20_L10", ti20)
 
     # mixed-state mana (Algorithm 6's W) of the Sec. 3.3.3 example: the 8-qutrit marginal (sites

@@ -164,13 +164,18 @@ hadamag_status hadamag_sre_mc(hadamag_ctx_t ctx, const void* psi_dev, int N, int
  * eps >= 0 (eps > 0 is needed when S(a) can vanish, e.g. stabilizer states).  means_out: L host
  * doubles or NULL.  traj_dev: NULL or L * (burn_in + n_s) int64 on the device, 8-byte aligned,
  * receiving traj[l * (burn_in + n_s) + t] = chain l's X-string after step t.
+ * stderr_out (host double or NULL): the statistical error of Eqs. Var_I_eps / m2error,
+ * delta M_2 = exp(-I) / ((exp(-I) - eps) ln 2) * sqrt(sum_l w_l^2 Var_l), with Var_l (the variance
+ * of chain l's mean, autocorrelation included) from non-overlapping batch means: B = min(32, n_s)
+ * batches of n_s div B consecutive recorded steps, Var_l = sum_b (m_b - mbar)^2 / (B (B - 1));
+ * 0 when n_s < 2.
  * Errors: NONFINITE when an evaluated S(a) + eps is 0 or the estimate is not finite.
  * Synchronises `stream`.
  */
 hadamag_status hadamag_sre_ti(hadamag_ctx_t ctx, const void* psi_dev, int N, int L, int64_t n_s,
                               int64_t burn_in, uint64_t seed, double eps, int sector,
-                              hadamag_dtype dtype, double* M2_out, double* means_out,
-                              int64_t* traj_dev, hadamag_stream_t stream);
+                              hadamag_dtype dtype, double* M2_out, double* stderr_out,
+                              double* means_out, int64_t* traj_dev, hadamag_stream_t stream);
 
 /*
  * Mana of an N-qutrit pure state, Eq. (mana2) of Sec. 2 evaluated by the per-X-string

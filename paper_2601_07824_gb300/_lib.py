@@ -74,7 +74,7 @@ def load(path: str | None = None):
             "hadamag_sre_batched": [V, I, PV, ctypes.POINTER(I), I, PV, V, V],
             "hadamag_sre_noalloc": [V, I, D, V, V],
             "hadamag_batched_status": [V, V],
-            "hadamag_sre_ti": [V, V, I, I, L, L, U64, D, I, I, PD, PD, V, V],
+            "hadamag_sre_ti": [V, V, I, I, L, L, U64, D, I, I, PD, PD, PD, V, V],
             "hadamag_sre_even_sector": [V, V, I, D, I, PD, PD, V],
             "hadamag_mana_qudit": [V, V, I, I, I, PD, PD, V],
             "hadamag_mana_grad": [V, V, I, I, I, PD, V, V],

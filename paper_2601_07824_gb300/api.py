@@ -144,21 +144,22 @@ def sre_even_sector(psi: torch.Tensor, n: float = 2.0, path: int | None = None):
 
 def sre_ti(psi: torch.Tensor, L: int, n_s: int, seed: int, burn_in: int = 0, eps: float = 0.0,
            record: bool = False, even_sector: bool = False):
-    """Thermodynamic-integration estimate of M_2 (Sec. 3.2, Algorithm 3): (M2_hat, chain means)
-    and, with record=True, the chains' X-strings after every step as an int64 tensor
-    [L, burn_in + n_s] on the state's device.  even_sector=True keeps the chains on
-    even-weight X-strings (U(1) or prod_j Z_j symmetric states)."""
+    """Thermodynamic-integration estimate of M_2 (Sec. 3.2, Algorithm 3): (M2_hat, delta M2, chain
+    means), delta M2 from Eq. m2error with batch-means variances; with record=True also the
+    chains' X-strings after every step as an int64 tensor [L, burn_in + n_s] on the state's
+    device.  even_sector=True keeps the chains on even-weight X-strings (U(1) or prod_j Z_j
+    symmetric states)."""
     N = _check_state(psi)
     c = _ctx(psi)
-    M = ctypes.c_double()
+    M, err = ctypes.c_double(), ctypes.c_double()
     means = (ctypes.c_double * int(L))()
     traj = torch.empty((int(L), int(burn_in) + int(n_s)), dtype=torch.int64, device=psi.device) if record else None
     c.check(c.lib.hadamag_sre_ti(c.h, ctypes.c_void_p(psi.data_ptr()), N, int(L), int(n_s), int(burn_in),
                                  ctypes.c_uint64(seed & (2 ** 64 - 1)), float(eps), 1 if even_sector else 0,
-                                 _dtype_code(psi), ctypes.byref(M), means,
+                                 _dtype_code(psi), ctypes.byref(M), ctypes.byref(err), means,
                                  ctypes.c_void_p(traj.data_ptr()) if record else None, _stream(psi)),
             "hadamag_sre_ti")
-    out = (M.value, list(means))
+    out = (M.value, err.value, list(means))
     return out + (traj,) if record else out
 
 

@@ -28,7 +28,8 @@ struct TiChains {
     int64_t* prop;        // [L] proposals: the X-string list handed to the per-X kernels
     double* f;            // [L] energy of the current X-string
     double* acc;          // [L] sum of the energies recorded after burn-in
-    double* out;          // [L + 2] chain means, I, M_2
+    double* out;          // [L + 3] chain means, I, M_2, delta M_2
+    double* bsum;         // [L][B] batch sums of the recorded energies (error estimate)
     const double* terms;  // [3L] per-X sums of the listed X-strings; S(a) at 3l
     int64_t* traj;        // [L][T] chain state after each step, or null
     int* status;
@@ -37,6 +38,8 @@ struct TiChains {
     int64_t T, burn_in, n_s;
     int L, N;
     int even;  // 1: chains restricted to even-weight X-strings
+    int B;     // batches per chain, K recorded steps each
+    int64_t K;
 };
 
 __device__ __forceinline__ double ti_energy(const TiChains& c, double S) {
@@ -60,6 +63,7 @@ __global__ void ti_init(TiChains c) {
     if (l >= c.L) return;
     c.f[l] = ti_energy(c, c.terms[3 * l]);
     c.acc[l] = 0.0;
+    for (int b = 0; b < c.B; ++b) c.bsum[(int64_t)l * c.B + b] = 0.0;
     c.prop[l] = c.a[l] ^ ti_move(c.seed, l, 0, c.N, c.even);
 }
 
@@ -76,22 +80,28 @@ __global__ void ti_step(TiChains c, int64_t t) {
         c.a[l] = a;
         c.f[l] = fa;
     }
-    if (t >= c.burn_in) c.acc[l] += fa;
+    if (t >= c.burn_in) {
+        c.acc[l] += fa;
+        const int64_t b = (t - c.burn_in) / c.K;
+        if (b < c.B) c.bsum[(int64_t)l * c.B + b] += fa;
+    }
     if (c.traj) c.traj[(int64_t)l * c.T + t] = a;
     if (t + 1 < c.T) c.prop[l] = a ^ ti_move(c.seed, l, t + 1, c.N, c.even);
 }
 
-// chain means, the quadrature I (fixed order) and M_2
+// chain means, the quadrature I, M_2 and its statistical error (fixed order)
 __global__ void ti_finish(TiChains c) {
     if (blockIdx.x != 0 || threadIdx.x != 0) return;
-    double I = 0.0;
+    double I = 0.0, var_I = 0.0;
     for (int l = 0; l < c.L; ++l) {
-        const double m = c.acc[l] / (double)c.n_s;
+        const double m = c.acc[l] / (double)c.n_s, w = ti_simpson_weight(l, c.L);
         c.out[l] = m;
-        I += ti_simpson_weight(l, c.L) * m;
+        I += w * m;
+        var_I += w * w * ti_chain_var(c.bsum + (int64_t)l * c.B, c.B, c.K);
     }
     c.out[c.L] = I;
     c.out[c.L + 1] = ti_m2(I, c.eps, c.even);
+    c.out[c.L + 2] = c.B < 2 ? 0.0 : ti_m2_slope(I, c.eps) * sqrt(var_I);
 }
 
 }  // namespace hm
@@ -100,8 +110,8 @@ using namespace hm;
 
 extern "C" hadamag_status hadamag_sre_ti(hadamag_ctx_t c, const void* psi, int N, int L, int64_t n_s,
                                          int64_t burn_in, uint64_t seed, double eps, int sector,
-                                         hadamag_dtype dt, double* M2_out, double* means_out,
-                                         int64_t* traj_dev, hadamag_stream_t stream) {
+                                         hadamag_dtype dt, double* M2_out, double* stderr_out,
+                                         double* means_out, int64_t* traj_dev, hadamag_stream_t stream) {
     if (!c) return HADAMAG_ERR_INVALID_ARG;
     if (!aligned16(psi) || !M2_out) return fail(c, HADAMAG_ERR_INVALID_ARG, "null or misaligned pointer");
     if (traj_dev && (reinterpret_cast<uintptr_t>(traj_dev) & 7))
@@ -120,7 +130,8 @@ extern "C" hadamag_status hadamag_sre_ti(hadamag_ctx_t c, const void* psi, int N
     if ((s = begin(c, st))) return s;
     const float2* p;
     if ((s = as_c64(c, psi, int64_t(1) << N, dt, st, &p))) return s;
-    if ((s = ensure_buf(c, c->ti_state, (size_t)(5 * L + 2) * 8))) return s;
+    const int B = ti_n_batches(n_s);
+    if ((s = ensure_buf(c, c->ti_state, (size_t)(5 * L + 3 + (size_t)L * B) * 8))) return s;
     if ((s = ensure_buf(c, c->terms, (size_t)L * 3 * sizeof(double)))) return s;
     char* base = (char*)c->ti_state.ptr;
     TiChains ch{};
@@ -129,6 +140,7 @@ extern "C" hadamag_status hadamag_sre_ti(hadamag_ctx_t c, const void* psi, int N
     ch.f = (double*)(base + (size_t)16 * L);
     ch.acc = (double*)(base + (size_t)24 * L);
     ch.out = (double*)(base + (size_t)32 * L);
+    ch.bsum = (double*)(base + (size_t)8 * (5 * L + 3));
     ch.terms = (const double*)c->terms.ptr;
     ch.traj = traj_dev;
     ch.status = (int*)c->status.ptr;
@@ -140,6 +152,8 @@ extern "C" hadamag_status hadamag_sre_ti(hadamag_ctx_t c, const void* psi, int N
     ch.L = L;
     ch.N = N;
     ch.even = sector;
+    ch.B = B;
+    ch.K = n_s / B;
     double* terms = (double*)c->terms.ptr;
     const unsigned grid = (unsigned)((L + 127) / 128);
     ti_start<<<grid, 128, 0, st>>>(ch);
@@ -158,7 +172,7 @@ extern "C" hadamag_status hadamag_sre_ti(hadamag_ctx_t c, const void* psi, int N
     ti_finish<<<1, 32, 0, st>>>(ch);
     c->launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "ti_finish");
-    std::vector<double> host((size_t)L + 2);
+    std::vector<double> host((size_t)L + 3);
     if ((e = cudaMemcpyAsync(host.data(), ch.out, host.size() * sizeof(double), cudaMemcpyDeviceToHost, st)) !=
         cudaSuccess)
         return cuda_fail(c, e, "copy chain means");
@@ -166,6 +180,7 @@ extern "C" hadamag_status hadamag_sre_ti(hadamag_ctx_t c, const void* psi, int N
     if (means_out)
         for (int l = 0; l < L; ++l) means_out[l] = host[l];
     *M2_out = host[(size_t)L + 1];
+    if (stderr_out) *stderr_out = host[(size_t)L + 2];
     if (!std::isfinite(*M2_out)) return fail(c, HADAMAG_ERR_NONFINITE, "non-finite estimate (I = %g)", host[L]);
     return HADAMAG_OK;
 }

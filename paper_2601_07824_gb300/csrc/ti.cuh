@@ -65,6 +65,30 @@ __host__ __device__ __forceinline__ double ti_simpson_weight(int l, int L) {
     return w;
 }
 
+// Statistical error (Eqs. Var_I_eps, m2error), Var[I] ~ sum_l w_l^2 2 tau_int sigma_f^2 / n_l,
+// estimated by non-overlapping batch means: the n_s recorded samples of a chain are cut into
+// B = min(32, n_s) batches of K = n_s div B consecutive samples (the remainder enters the mean
+// only) and Var_l = sum_b (m_b - mbar)^2 / (B (B - 1)); delta M_2 = (d M_2 / d I) sqrt(Var[I]).
+__host__ __device__ __forceinline__ int ti_n_batches(int64_t n_s) { return n_s < 32 ? (int)n_s : 32; }
+
+__host__ __device__ inline double ti_chain_var(const double* bsum, int B, int64_t K) {
+    if (B < 2) return 0.0;
+    double mbar = 0.0;
+    for (int b = 0; b < B; ++b) mbar += bsum[b] / (double)K;
+    mbar /= (double)B;
+    double v = 0.0;
+    for (int b = 0; b < B; ++b) {
+        const double d = bsum[b] / (double)K - mbar;
+        v += d * d;
+    }
+    return v / ((double)B * (double)(B - 1));
+}
+
+// d M_2 / d I for M_2 = -log2(exp(-I) - eps) (+ const)
+__host__ __device__ __forceinline__ double ti_m2_slope(double I, double eps) {
+    return exp(-I) / ((exp(-I) - eps) * 0.693147180559945309417);
+}
+
 // M_2 from the quadrature I of the chain means, I = ln Z_0 - ln Z_1 with Z_1 = S_2 + Z_0 eps:
 // Z_0 = 2^N gives -log2(exp(-I) - eps); the even sector (Z_0 = 2^(N-1)) adds 1
 __host__ __device__ __forceinline__ double ti_m2(double I, double eps, int even) {

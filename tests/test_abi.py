@@ -70,8 +70,8 @@ def test_typed_binding_marshals_every_argument_without_gpu():
     from paper_2601_07824_gb300 import _lib
     lib = _lib.load()
     M, means = C.c_double(), (C.c_double * 4)()
-    assert lib.hadamag_sre_ti(None, None, 10, 4, 100, 10, C.c_uint64(2 ** 64 - 1), 0.0, 1, 0, C.byref(M), means,
-                              None, None) == 1
+    assert lib.hadamag_sre_ti(None, None, 10, 4, 100, 10, C.c_uint64(2 ** 64 - 1), 0.0, 1, 0, C.byref(M), C.byref(M),
+                              means, None, None) == 1
     assert lib.hadamag_sre_even_sector(None, None, 10, 2.0, 0, C.byref(M), C.byref(M), None) == 1
     assert lib.hadamag_mana_mixed(None, None, 4, 0, C.byref(M), means, None) == 1
     assert lib.hadamag_reduced_density_matrix(None, None, 4, 0, (C.c_int * 2)(0, 1), 2, None, None) == 1

@@ -48,13 +48,14 @@ def move_mask(r, N, sector):
 def check_against_oracle(psi_np, L, n_s, burn, seed, eps=0.0, sector=None):
     N = int(psi_np.size).bit_length() - 1
     psi = torch.from_numpy(psi_np).to(DEV)
-    M2, means, traj = hm.sre_ti(psi, L, n_s, seed, burn_in=burn, eps=eps, record=True,
-                                even_sector=sector == "even")
+    M2, err, means, traj = hm.sre_ti(psi, L, n_s, seed, burn_in=burn, eps=eps, record=True,
+                                     even_sector=sector == "even")
     traj = traj.cpu().numpy()
     rec = {}
     f = ti.energy_table(psi_np, eps, sector) if N <= 12 else ti.energy_fn(psi_np, eps)
     means_o, _ = ti.metropolis_means(f, N, L, n_s, seed, burn, record=rec, sector=sector)
-    M2_o = ti.m2_from_integral(float(np.dot(ti.simpson_weights(L), means_o)), eps, sector)
+    I_o = float(np.dot(ti.simpson_weights(L), means_o))
+    M2_o = ti.m2_from_integral(I_o, eps, sector)
     T = burn + n_s
     assert traj.shape == (L, T)
     parted = []
@@ -78,6 +79,8 @@ def check_against_oracle(psi_np, L, n_s, burn, seed, eps=0.0, sector=None):
             assert means[l] == pytest.approx(means_o[l], abs=TOL_F), l
     if not parted:
         assert M2 == pytest.approx(M2_o, abs=TOL_M)
+        # batch means move by at most 2 TOL_F, the error by at most 2 TOL_F / (sqrt(B - 1) ln 2)
+        assert err == pytest.approx(ti.m2_stderr(rec["batch_sums"], n_s, I_o, eps), abs=TOL_M)
     return M2, M2_o, parted
 
 
@@ -126,11 +129,11 @@ def test_even_sector_invalid_for_one_qubit():
 def test_complex128_input_and_unrecorded_run():
     psi_np = I.gaussian_state(12, 3300)
     psi = torch.from_numpy(psi_np).to(DEV)
-    M2a, means_a, _ = hm.sre_ti(psi, 5, 200, 11, burn_in=10, record=True)
-    M2b, means_b = hm.sre_ti(psi, 5, 200, 11, burn_in=10)  # no trajectory buffer
-    assert M2a == M2b and means_a == means_b
+    M2a, erra, means_a, _ = hm.sre_ti(psi, 5, 200, 11, burn_in=10, record=True)
+    M2b, errb, means_b = hm.sre_ti(psi, 5, 200, 11, burn_in=10)  # no trajectory buffer
+    assert M2a == M2b and erra == errb and means_a == means_b and erra > 0.0
     # the GPU reads complex128 input rounded to complex64: same chains as the complex64 state
-    M2c, _ = hm.sre_ti(psi.to(torch.complex64), 5, 200, 11, burn_in=10)
+    M2c, _, _ = hm.sre_ti(psi.to(torch.complex64), 5, 200, 11, burn_in=10)
     assert M2c == M2a
     M2_o = ti.m2_metropolis(psi_np.astype(np.complex64), 5, 200, 11, burn_in=10)
     assert M2a == pytest.approx(M2_o, abs=TOL_M)
@@ -160,5 +163,6 @@ def test_vanishing_energy_and_invalid_arguments():
             hm.sre_ti(psi, args.pop("L"), args.pop("n_s"), **args)
         assert e.value.code == 1
     # the context stays usable
-    M2, _ = hm.sre_ti(psi, 3, 20, 1)
-    assert np.isfinite(M2)
+    M2, err, _ = hm.sre_ti(psi, 3, 20, 1)
+    assert np.isfinite(M2) and err > 0.0
+    assert hm.sre_ti(psi, 3, 1, 1)[1] == 0.0  # one recorded step: no error estimate

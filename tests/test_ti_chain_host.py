@@ -1,7 +1,8 @@
 """The thermodynamic-integration kernels' per-chain arithmetic (ti.cuh: start pattern, moves,
-acceptance variate, beta grid, decision, Simpson weights, M_2), compiled for the host and run
-in the kernels' order on exact FP64 energies, must give the oracle's chains (Algorithm 3)
-step for step and the same means and M_2.  CPU only: needs nvcc, no GPU."""
+acceptance variate, beta grid, decision, Simpson weights, M_2, batch-means error), compiled for
+the host and run in the kernels' order on exact FP64 energies, must give the oracle's chains
+(Algorithm 3) step for step and the same means, M_2 and delta M_2.  CPU only: needs nvcc, no
+GPU."""
 import os
 import shutil
 import subprocess
@@ -55,8 +56,8 @@ def test_kernel_chain_arithmetic_reproduces_the_oracle(replay, label, make, L, n
                     "1" if sector else "0", ofile], check=True)
     raw = open(ofile, "rb").read()
     nonpos = int(np.frombuffer(raw[:4], dtype=np.int32)[0])
-    out = np.frombuffer(raw[4:4 + 8 * (L + 2)], dtype=np.float64)
-    traj = np.frombuffer(raw[4 + 8 * (L + 2):], dtype=np.int64).reshape(L, burn + n_s)
+    out = np.frombuffer(raw[4:4 + 8 * (L + 3)], dtype=np.float64)
+    traj = np.frombuffer(raw[4 + 8 * (L + 3):], dtype=np.int64).reshape(L, burn + n_s)
     rec = {}
     means, _ = ti.metropolis_means(ti.energy_table(psi, eps, sector), N, L, n_s, seed, burn, record=rec,
                                    sector=sector)
@@ -66,6 +67,7 @@ def test_kernel_chain_arithmetic_reproduces_the_oracle(replay, label, make, L, n
     np.testing.assert_allclose(out[:L], means, rtol=0, atol=1e-12)
     assert out[L] == pytest.approx(I_, abs=1e-12)
     assert out[L + 1] == pytest.approx(ti.m2_from_integral(I_, eps, sector), abs=1e-12)
+    assert out[L + 2] == pytest.approx(ti.m2_stderr(rec["batch_sums"], n_s, I_, eps), rel=1e-10, abs=1e-15)
 
 
 def test_vanishing_sum_is_flagged(replay):

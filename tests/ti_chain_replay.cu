@@ -4,7 +4,7 @@
 // per-X kernels.  Used by tests/test_ti_chain_host.py to compare the chains with the oracle's.
 //
 // usage: ti_chain_replay S.bin N L n_s burn_in seed eps even out.bin
-// out.bin: int32 nonpos flag, (L + 2) doubles (means, I, M_2), L * T int64 trajectory.
+// out.bin: int32 nonpos flag, (L + 3) doubles (means, I, M_2, delta M_2), L * T int64 trajectory.
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -27,7 +27,9 @@ int main(int argc, char** argv) {
     fclose(f);
     const long long T = burn + n_s;
     std::vector<long long> a(L), prop(L), traj((size_t)L * T);
-    std::vector<double> fe(L), acc(L), out(L + 2);
+    const int B = ti_n_batches(n_s);
+    const long long K = n_s / B;
+    std::vector<double> fe(L), acc(L), out(L + 3), bsum((size_t)L * B, 0.0);
     int nonpos = 0;
     auto energy = [&](double s) {
         const double x = s + eps;
@@ -54,17 +56,24 @@ int main(int argc, char** argv) {
                 a[l] = x;
                 fe[l] = fa;
             }
-            if (t >= burn) acc[l] += fa;
+            if (t >= burn) {
+                acc[l] += fa;
+                const long long b = (t - burn) / K;
+                if (b < B) bsum[(size_t)l * B + b] += fa;
+            }
             traj[(size_t)l * T + t] = x;
             if (t + 1 < T) prop[l] = x ^ ti_move(seed, l, t + 1, N, even);
         }
-    double I = 0.0;  // ti_finish
+    double I = 0.0, var_I = 0.0;  // ti_finish
     for (int l = 0; l < L; ++l) {
+        const double w = ti_simpson_weight(l, L);
         out[l] = acc[l] / (double)n_s;
-        I += ti_simpson_weight(l, L) * out[l];
+        I += w * out[l];
+        var_I += w * w * ti_chain_var(bsum.data() + (size_t)l * B, B, K);
     }
     out[L] = I;
     out[L + 1] = ti_m2(I, eps, even);
+    out[L + 2] = B < 2 ? 0.0 : ti_m2_slope(I, eps) * sqrt(var_I);
     FILE* o = fopen(argv[9], "wb");
     if (!o) return 4;
     fwrite(&nonpos, sizeof(int), 1, o);
