@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--extra", action="store_true",
                     help="also time N=22, mana N=11, MC N=28, batched, thermodynamic integration N=20, "
                          "mixed-state mana N=8, even-sector SRE N=20, qudit mana d=5, mana gradient")
+    ap.add_argument("--only", default="",
+                    help="profiling aid: run just the named --extra workload (e.g. ti_N20_L10) and print it")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--xstrings", type=int, default=0,
                     help="profiling aid: each step evaluates only the first K X-strings of the "
@@ -276,6 +278,13 @@ def main():
             dist.barrier()
         torch.cuda.synchronize(dev)
 
+    if args.only:
+        if rank == 0:
+            print(json.dumps({"extra": extra_workloads(hm, dev, sm_count, args.only)}), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
     M = ln = None
     if args.xstrings > 0:
         alist = torch.arange(args.xstrings, dtype=torch.int64, device=dev)
@@ -370,8 +379,9 @@ def main():
         dist.destroy_process_group()
 
 
-def extra_workloads(hm, dev, sm_count):
-    """The other configurations, one timed call each (not part of the headline value)."""
+def extra_workloads(hm, dev, sm_count, only: str = ""):
+    """The other configurations, one timed call each (not part of the headline value); with
+    `only`, just the workload of that name."""
     import numpy as np
     import torch
     from paper_2601_07824_gb300 import _lib, inputs
@@ -388,6 +398,8 @@ def extra_workloads(hm, dev, sm_count):
         return (time.perf_counter() - t0) / reps, r
 
     def guard(key, fn):
+        if only and key != only:
+            return
         try:
             out[key] = fn()
         except Exception as e:  # noqa: BLE001
@@ -396,7 +408,8 @@ def extra_workloads(hm, dev, sm_count):
     tpeak, tsrc = measured_peak("bf16_tflops_sustained", 1700.0)
 
     # exact M2 at N = 22 (Gaussian state): FP32 CUDA-core path vs tensor-core path
-    psi22 = torch.from_numpy(inputs.gaussian_state(22, 2201, dtype=np.complex64)).to(dev)
+    psi22 = torch.from_numpy(inputs.gaussian_state(22, 2201, dtype=np.complex64)).to(dev) \
+        if not only or only.startswith("sre_N22") else None
     res = {}
     for name, p in (("cudacore", _lib.PATH_CUDACORE), ("tensor", _lib.PATH_TENSOR)):
         def run22(p=p, name=name):
