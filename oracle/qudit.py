@@ -72,6 +72,33 @@ def wigner_brute(psi, d: int) -> np.ndarray:
     return np.array([np.vdot(psi, A @ psi) for A in As]) / d ** N
 
 
+def wigner_mixed_brute(rho, d: int) -> np.ndarray:
+    """W(u) = tr(A_u rho) / d^N for a density matrix (dense operators, N small)."""
+    rho = np.asarray(rho, dtype=np.complex128)
+    N = n_sites(rho.shape[0], d)
+    As, _ = phase_point_operators(N, d)
+    return np.array([np.trace(A @ rho) for A in As]) / d ** N
+
+
+def mana_mixed_fast(rho, d: int, chunk: int = 256):
+    """(mana, sum |W|, sum W, sum W^2) of a density matrix by the per-shift transform with the
+    gather v_x = rho[-x - a, x - a] (digit-wise mod d; for rho = |psi><psi| this is
+    conj(psi_{x-a}) psi_{-x-a}), F_d^{(x)N} and W = chi / d^N (a relabelling of u)."""
+    _check_d(d)
+    rho = np.asarray(rho, dtype=np.complex128)
+    D = rho.shape[0]
+    N = n_sites(D, d)
+    dig, pw = _digits(D, N, d), d ** np.arange(N)
+    s_abs = s1 = s2 = 0.0
+    for a0 in range(0, D, chunk):
+        i1, i2 = _shift_indices(dig, dig[a0:a0 + chunk], d, pw)
+        chi = _transform_rows(rho[i2, i1], d, N).real / d ** N
+        s_abs += float(np.abs(chi).sum())
+        s1 += float(chi.sum())
+        s2 += float((chi ** 2).sum())
+    return float(np.log2(s_abs)), s_abs, s1, s2
+
+
 def mana_brute(psi, d: int):
     W = wigner_brute(psi, d)
     s = float(np.abs(W.real).sum())

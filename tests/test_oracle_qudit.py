@@ -122,3 +122,35 @@ def test_mana_gradient_counts_small_entries():
     _, _, kall = Q.mana_grad(psi, 5, small=1e9)
     assert k0 == 0 and kall == 5 ** 4
     assert m0 == m and np.array_equal(g0, g)
+
+
+# ---- mixed states ---------------------------------------------------------------------
+
+def _random_rho(D, rank, seed):
+    rng = np.random.default_rng(seed)
+    G = rng.normal(size=(D, rank)) + 1j * rng.normal(size=(D, rank))
+    r = G @ G.conj().T
+    return r / np.trace(r).real
+
+
+@pytest.mark.parametrize("d,N", [(3, 2), (5, 1), (5, 2), (7, 1), (11, 1)])
+def test_mixed_transform_equals_dense_definition(d, N):
+    D = d ** N
+    for rank in sorted({1, 2, D}):
+        rho = _random_rho(D, rank, 40 * d + rank)
+        W = Q.wigner_mixed_brute(rho, d)
+        assert np.abs(W.imag).max() < 1e-14
+        m, s, s1, s2 = Q.mana_mixed_fast(rho, d)
+        assert s == pytest.approx(float(np.abs(W.real).sum()), rel=1e-12)
+        assert m == pytest.approx(float(np.log2(np.abs(W.real).sum())), abs=1e-12)
+        assert s1 == pytest.approx(1.0, abs=1e-12)                                   # sum W = tr rho
+        assert s2 * d ** N == pytest.approx(float(np.trace(rho @ rho).real), rel=1e-10)  # d^N sum W^2 = tr rho^2
+
+
+@pytest.mark.parametrize("d,N", [(5, 2), (7, 2), (13, 1)])
+def test_mixed_reduces_to_pure_and_maximally_mixed_is_zero(d, N):
+    psi = I.gaussian_state(N, 60 + d, d=d)
+    assert Q.mana_mixed_fast(np.outer(psi, psi.conj()), d)[0] == pytest.approx(Q.mana_fast(psi, d)[0], abs=1e-12)
+    D = d ** N
+    m, s, _, _ = Q.mana_mixed_fast(np.eye(D) / D, d)
+    assert abs(m) < 1e-12 and s == pytest.approx(1.0, abs=1e-12)
