@@ -241,6 +241,17 @@ hadamag_status hadamag_mana_mixed(hadamag_ctx_t ctx, const void* rho_dev, int N,
                                   double* mana_out, double* sums_out, hadamag_stream_t stream);
 
 /*
+ * hadamag_mana_mixed for N qudits of odd prime dimension d (Sec. 2: the construction holds for
+ * any odd prime d): rho_dev is d^N x d^N complex (dtype), row-major, qudit j = base-d digit j;
+ * v_x = rho[-x - a, x - a] digit-wise mod d, F_d^{(x)N} with (F_d)_jk = w^{2jk}, W = chi / d^N.
+ * d = 3 is hadamag_mana_mixed (N <= 10); d = 5, 7, 11, 13 need d^N <= 25600 (N <= 6, 5, 4, 3);
+ * other d give UNSUPPORTED.  sums_out as for hadamag_mana_mixed.  Synchronises `stream`.
+ */
+hadamag_status hadamag_mana_mixed_qudit(hadamag_ctx_t ctx, const void* rho_dev, int N, int d,
+                                        hadamag_dtype dtype, double* mana_out, double* sums_out,
+                                        hadamag_stream_t stream);
+
+/*
  * Reduced density matrix of an N-qutrit pure state (the partial trace that gives the mixed
  * states of Sec. 3.3.3):  rho_A[r, c] = sum_x psi[(r, x)] conj(psi[(c, x)]), where site keep[m]
  * is base-3 digit m of r and c and x runs over the other sites.  keep: n_keep distinct sites

@@ -202,23 +202,26 @@ def mana_grad(psi: torch.Tensor, d: int = 3):
     return m.value, grad
 
 
-def mana_mixed(rho: torch.Tensor):
-    """(mana in bits, [sum |chi|, sum chi, sum chi^2]) of an N-qutrit density matrix given as a
-    3^N x 3^N CUDA tensor (Algorithm 6's W via the Algorithm 5 transform, Sec. 3.3.3)."""
+def mana_mixed(rho: torch.Tensor, d: int = 3):
+    """(mana in bits, [sum |chi|, sum chi, sum chi^2]) of a density matrix of N qudits (d = 3:
+    qutrits, Algorithm 6's W via the Algorithm 5 transform, Sec. 3.3.3; other odd primes d as
+    Sec. 2 allows) given as a d^N x d^N CUDA tensor."""
+    if int(d) < 2:
+        raise ValueError("d must be an odd prime")
     if not isinstance(rho, torch.Tensor) or not rho.is_cuda:
         raise TypeError("rho must be a CUDA tensor")
     if rho.dim() != 2 or rho.shape[0] != rho.shape[1] or not rho.is_contiguous():
         raise ValueError("rho must be a contiguous square matrix")
     n, D = 0, rho.shape[0]
-    while 3 ** n < D:
+    while d ** n < D:
         n += 1
-    if 3 ** n != D or n < 1:
-        raise ValueError(f"rho must be 3^N x 3^N, got {D} x {D}")
+    if d ** n != D or n < 1:
+        raise ValueError(f"rho must be {d}^N x {d}^N, got {D} x {D}")
     c = _ctx(rho)
     m = ctypes.c_double()
     sums = (ctypes.c_double * 3)()
-    c.check(c.lib.hadamag_mana_mixed(c.h, ctypes.c_void_p(rho.data_ptr()), n, _dtype_code(rho), ctypes.byref(m),
-                                     sums, _stream(rho)), "hadamag_mana_mixed")
+    c.check(c.lib.hadamag_mana_mixed_qudit(c.h, ctypes.c_void_p(rho.data_ptr()), n, int(d), _dtype_code(rho),
+                                           ctypes.byref(m), sums, _stream(rho)), "hadamag_mana_mixed_qudit")
     return m.value, list(sums)
 
 

@@ -40,6 +40,9 @@ cudaError_t launch_mana_qudit(const float2* psi, int N, int d, double* out, int 
                               cudaStream_t st);
 cudaError_t launch_mana_grad(const float2* psi, int N, int d, double* out, double2* gpart, int sm_count, int max_grid,
                              int* grid, cudaStream_t st);
+// the mana launch for a d^N x d^N density matrix (row-major), v_x = rho[-x - a, x - a]
+cudaError_t launch_mana_qudit_mixed(const float2* rho, int N, int d, double* out, int sm_count, int max_grid,
+                                    int* grid, cudaStream_t st);
 cudaError_t launch_mana_grad_finalize(const double2* gpart, int parts, int dim, const double* msum, void* grad,
                                       bool c128, cudaStream_t st);
 

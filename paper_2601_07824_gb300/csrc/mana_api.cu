@@ -143,6 +143,41 @@ extern "C" hadamag_status hadamag_mana_qudit(hadamag_ctx_t c, const void* psi, i
     return HADAMAG_OK;
 }
 
+extern "C" hadamag_status hadamag_mana_mixed_qudit(hadamag_ctx_t c, const void* rho, int N, int d, hadamag_dtype dt,
+                                                   double* mana_out, double* sums_out, hadamag_stream_t stream) {
+    if (!c) return HADAMAG_ERR_INVALID_ARG;
+    if (d == 3) return hadamag_mana_mixed(c, rho, N, dt, mana_out, sums_out, stream);
+    if (!aligned16(rho)) return fail(c, HADAMAG_ERR_INVALID_ARG, "null or misaligned pointer");
+    if (dt != HADAMAG_C64 && dt != HADAMAG_C128) return fail(c, HADAMAG_ERR_INVALID_ARG, "bad dtype");
+    const int nmax = mana_qudit_max_n(d);
+    if (nmax == 0) return fail(c, HADAMAG_ERR_UNSUPPORTED, "d must be 3, 5, 7, 11 or 13 (got %d)", d);
+    if (N < 1 || N > nmax) return fail(c, HADAMAG_ERR_INVALID_ARG, "N must be in [1, %d] for d = %d (got %d)", nmax, d, N);
+    cudaStream_t st = reinterpret_cast<cudaStream_t>(stream);
+    hadamag_status s;
+    cudaError_t e;
+    if ((s = begin(c, st))) return s;
+    int64_t dim = 1;
+    for (int j = 0; j < N; ++j) dim *= d;
+    const float2* p;
+    if ((s = as_c64(c, rho, dim * dim, dt, st, &p))) return s;
+    const int max_grid = c->sm_count * 8;
+    if ((s = ensure_buf(c, c->part, (size_t)max_grid * 3 * sizeof(double)))) return s;
+    int grid = 0;
+    e = launch_mana_qudit_mixed(p, N, d, (double*)c->part.ptr, c->sm_count, max_grid, &grid, st);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(c, e, "mana_qudit_mixed");
+    e = launch_sum_triples((const double*)c->part.ptr, grid, (double*)c->res.ptr, st);
+    c->launches++;
+    if (e != cudaSuccess) return cuda_fail(c, e, "sum_triples");
+    if ((s = finish(c, (const double*)c->res.ptr, 3, st))) return s;
+    double m = std::log2(c->host_res[0] / (double)dim);
+    if (m == 0.0) m = 0.0;
+    if (mana_out) *mana_out = m;
+    if (sums_out) { sums_out[0] = c->host_res[0]; sums_out[1] = c->host_res[1]; sums_out[2] = c->host_res[2]; }
+    if (!std::isfinite(m)) return fail(c, HADAMAG_ERR_NONFINITE, "non-finite mana");
+    return HADAMAG_OK;
+}
+
 extern "C" hadamag_status hadamag_mana_grad(hadamag_ctx_t c, const void* psi, int N, int d, hadamag_dtype dt,
                                             double* mana_out, void* grad, hadamag_stream_t stream) {
     if (!c) return HADAMAG_ERR_INVALID_ARG;

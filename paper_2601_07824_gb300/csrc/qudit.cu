@@ -85,7 +85,9 @@ __device__ __forceinline__ void qudit_cta_sum(float m, float s1, float q, float 
         for (int w = 0; w < (int)(blockDim.x >> 5); ++w) { acc[0] += red[w][0]; acc[1] += red[w][1]; acc[2] += red[w][2]; }
 }
 
-template <int D>
+// MIXED: psi is a density matrix rho (dim x dim, row-major) and v_x = rho[-x - a, x - a], which
+// for rho = |psi><psi| is conj(psi_{x-a}) psi_{-x-a}; every entry of rho is read once.
+template <int D, bool MIXED>
 __global__ void __launch_bounds__(256) mana_qudit_kernel(const float2* __restrict__ psi, int N, int dim,
                                                          double* __restrict__ out) {
     extern __shared__ float2 v[];  // dim values
@@ -101,7 +103,8 @@ __global__ void __launch_bounds__(256) mana_qudit_kernel(const float2* __restric
         for (int x = tid; x < dim; x += blockDim.x) {
             int i1, i2;
             qudit_pair_idx<D>(x, ad, N, i1, i2);
-            v[x] = conj_mul(__ldg(psi + i1), __ldg(psi + i2));
+            if constexpr (MIXED) v[x] = __ldg(psi + (int64_t)i2 * dim + i1);
+            else v[x] = conj_mul(__ldg(psi + i1), __ldg(psi + i2));
         }
         qudit_transform<D>(v, tw, N, dim);
         float m = 0.f, s1 = 0.f, q = 0.f;
@@ -190,7 +193,7 @@ int mana_qudit_max_n(int d) {
     return n < QUDIT_MAXN ? n : QUDIT_MAXN;
 }
 
-template <int D, bool GRAD>
+template <int D, bool GRAD, bool MIXED>
 static cudaError_t launch_qudit_d(const float2* psi, int N, int dim, double* out, double2* gpart, int sm_count,
                                   int max_grid, int* grid, cudaStream_t st) {
     const size_t smem = (size_t)dim * sizeof(float2);
@@ -202,10 +205,10 @@ static cudaError_t launch_qudit_d(const float2* psi, int N, int dim, double* out
             return e;
         e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mana_grad_kernel<D>, 256, smem);
     } else {
-        if ((e = cudaFuncSetAttribute(mana_qudit_kernel<D>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem)) !=
-            cudaSuccess)
+        if ((e = cudaFuncSetAttribute(mana_qudit_kernel<D, MIXED>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                      (int)smem)) != cudaSuccess)
             return e;
-        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mana_qudit_kernel<D>, 256, smem);
+        e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, mana_qudit_kernel<D, MIXED>, 256, smem);
     }
     if (e != cudaSuccess) return e;
     int g = (occ < 1 ? 1 : occ) * sm_count;
@@ -213,34 +216,39 @@ static cudaError_t launch_qudit_d(const float2* psi, int N, int dim, double* out
     if (g > max_grid) g = max_grid;
     *grid = g;
     if constexpr (GRAD) mana_grad_kernel<D><<<g, 256, smem, st>>>(psi, N, dim, out, gpart);
-    else mana_qudit_kernel<D><<<g, 256, smem, st>>>(psi, N, dim, out);
+    else mana_qudit_kernel<D, MIXED><<<g, 256, smem, st>>>(psi, N, dim, out);
     return cudaGetLastError();
 }
 
-template <bool GRAD>
+template <bool GRAD, bool MIXED>
 static cudaError_t launch_qudit(const float2* psi, int N, int d, double* out, double2* gpart, int sm_count,
                                 int max_grid, int* grid, cudaStream_t st) {
     if (N < 1 || N > mana_qudit_max_n(d)) return cudaErrorInvalidValue;
     int dim = 1;
     for (int j = 0; j < N; ++j) dim *= d;
     switch (d) {
-        case 3: return launch_qudit_d<3, GRAD>(psi, N, dim, out, gpart, sm_count, max_grid, grid, st);
-        case 5: return launch_qudit_d<5, GRAD>(psi, N, dim, out, gpart, sm_count, max_grid, grid, st);
-        case 7: return launch_qudit_d<7, GRAD>(psi, N, dim, out, gpart, sm_count, max_grid, grid, st);
-        case 11: return launch_qudit_d<11, GRAD>(psi, N, dim, out, gpart, sm_count, max_grid, grid, st);
-        case 13: return launch_qudit_d<13, GRAD>(psi, N, dim, out, gpart, sm_count, max_grid, grid, st);
+        case 3: return launch_qudit_d<3, GRAD, MIXED>(psi, N, dim, out, gpart, sm_count, max_grid, grid, st);
+        case 5: return launch_qudit_d<5, GRAD, MIXED>(psi, N, dim, out, gpart, sm_count, max_grid, grid, st);
+        case 7: return launch_qudit_d<7, GRAD, MIXED>(psi, N, dim, out, gpart, sm_count, max_grid, grid, st);
+        case 11: return launch_qudit_d<11, GRAD, MIXED>(psi, N, dim, out, gpart, sm_count, max_grid, grid, st);
+        case 13: return launch_qudit_d<13, GRAD, MIXED>(psi, N, dim, out, gpart, sm_count, max_grid, grid, st);
         default: return cudaErrorInvalidValue;
     }
 }
 
 cudaError_t launch_mana_qudit(const float2* psi, int N, int d, double* out, int sm_count, int max_grid, int* grid,
                               cudaStream_t st) {
-    return launch_qudit<false>(psi, N, d, out, nullptr, sm_count, max_grid, grid, st);
+    return launch_qudit<false, false>(psi, N, d, out, nullptr, sm_count, max_grid, grid, st);
+}
+
+cudaError_t launch_mana_qudit_mixed(const float2* rho, int N, int d, double* out, int sm_count, int max_grid,
+                                    int* grid, cudaStream_t st) {
+    return launch_qudit<false, true>(rho, N, d, out, nullptr, sm_count, max_grid, grid, st);
 }
 
 cudaError_t launch_mana_grad(const float2* psi, int N, int d, double* out, double2* gpart, int sm_count, int max_grid,
                              int* grid, cudaStream_t st) {
-    return launch_qudit<true>(psi, N, d, out, gpart, sm_count, max_grid, grid, st);
+    return launch_qudit<true, false>(psi, N, d, out, gpart, sm_count, max_grid, grid, st);
 }
 
 cudaError_t launch_mana_grad_finalize(const double2* gpart, int parts, int dim, const double* msum, void* grad,

@@ -133,3 +133,30 @@ def test_mana_gradient_invalid_arguments():
     assert e.value.code == 1
     with pytest.raises(ValueError):
         hm.mana_grad(buf[:10].contiguous(), 3)
+
+
+# ---- mixed states of qudits -----------------------------------------------------------
+
+@pytest.mark.parametrize("d,N", [(5, 1), (5, 2), (5, 3), (7, 2), (11, 2), (13, 2)])
+def test_mixed_qudit_states_vs_oracle(d, N):
+    D = d ** N
+    rng = np.random.default_rng(4000 + d + N)
+    for rank in sorted({1, 3, D}):
+        G = rng.normal(size=(D, rank)) + 1j * rng.normal(size=(D, rank))
+        rho = G @ G.conj().T
+        rho = (rho / np.trace(rho).real).astype(np.complex64)
+        m, sums = hm.mana_mixed(on_dev(rho), d)
+        mo, so, s1, s2 = Q.mana_mixed_fast(rho.astype(np.complex128), d)
+        assert abs(m - mo) <= 1e-6 * max(1.0, abs(mo)), (d, N, rank, m, mo)
+        assert abs(sums[1] / D - s1) < 1e-5 and abs(sums[2] / D - s2 * D) < 1e-5  # tr rho, tr rho^2
+
+
+@pytest.mark.parametrize("d,N", [(5, 4), (7, 3)])
+def test_mixed_qudit_pure_and_maximally_mixed(d, N):
+    psi = I.gaussian_state(N, 4100 + d, d=d, dtype=np.complex64)
+    p = on_dev(psi)
+    m, _ = hm.mana_mixed(torch.outer(p, p.conj()).contiguous(), d)
+    assert abs(m - hm.mana_qudit(p, d)[0]) <= 1e-6 * max(1.0, abs(m))
+    D = d ** N
+    mm, _ = hm.mana_mixed(on_dev(np.eye(D, dtype=np.complex64) / D), d)
+    assert abs(mm) <= stab_tol(d, N)
