@@ -262,6 +262,11 @@ hadamag_status hadamag_mana_mixed_qudit(hadamag_ctx_t ctx, const void* rho_dev, 
 hadamag_status hadamag_reduced_density_matrix(hadamag_ctx_t ctx, const void* psi_dev, int N,
                                               hadamag_dtype dtype, const int* keep, int n_keep,
                                               void* rho_dev, hadamag_stream_t stream);
+/* The same for sites of dimension d (2 <= d <= 13): psi_dev has d^N amplitudes (site j = base-d
+ * digit j), d^N <= 3^16 and d^n_keep <= 3^10; rho_dev is d^n_keep x d^n_keep complex64. */
+hadamag_status hadamag_reduced_density_matrix_qudit(hadamag_ctx_t ctx, const void* psi_dev, int N, int d,
+                                                    hadamag_dtype dtype, const int* keep, int n_keep,
+                                                    void* rho_dev, hadamag_stream_t stream);
 
 /*
  * M_2 and its Wirtinger gradient dM_2/dpsi* (not in the paper; it is what magic

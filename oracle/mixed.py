@@ -26,30 +26,31 @@ import numpy as np
 from . import brute
 
 
-def _n_sites(dim: int) -> int:
+def _n_sites(dim: int, d: int = 3) -> int:
     N = 0
-    while 3 ** N < dim:
+    while d ** N < dim:
         N += 1
-    if 3 ** N != dim:
-        raise ValueError("dimension must be 3^N")
+    if d ** N != dim:
+        raise ValueError(f"dimension must be {d}^N")
     return N
 
 
-def reduced_density_matrix(psi, keep) -> np.ndarray:
-    """rho_A = tr_B |psi><psi| for the sites in `keep` (site keep[m] becomes digit m of rho_A).
+def reduced_density_matrix(psi, keep, d: int = 3) -> np.ndarray:
+    """rho_A = tr_B |psi><psi| for the sites in `keep` (site keep[m] becomes digit m of rho_A),
+    for sites of dimension d (qutrits by default).
 
     The partial trace of Sec. 4.3's mixed-state example, written out: rho_A[r, c] =
     sum_x psi[(r, x)] conj(psi[(c, x)]) over the digits x of the traced-out sites."""
     psi = np.asarray(psi, dtype=np.complex128).ravel()
-    N = _n_sites(psi.size)
+    N = _n_sites(psi.size, d)
     keep = list(keep)
     if len(set(keep)) != len(keep) or any(k < 0 or k >= N for k in keep):
         raise ValueError("keep must list distinct sites in [0, N)")
     rest = [k for k in range(N) if k not in keep]
     # axis t of the reshaped tensor is site N-1-t (the most significant digit comes first)
-    t = psi.reshape((3,) * N) if N else psi.reshape(())
+    t = psi.reshape((d,) * N) if N else psi.reshape(())
     order = [N - 1 - k for k in reversed(keep)] + [N - 1 - k for k in reversed(rest)]
-    m = np.transpose(t, order).reshape(3 ** len(keep), 3 ** len(rest))
+    m = np.transpose(t, order).reshape(d ** len(keep), d ** len(rest))
     return m @ m.conj().T
 
 

@@ -26,7 +26,7 @@ EXPORTS = [
     "hadamag_mana", "hadamag_mana_sums", "hadamag_sre_grad", "hadamag_sre_batched",
     "hadamag_sre_noalloc", "hadamag_batched_status", "hadamag_sre_ti", "hadamag_mana_mixed",
     "hadamag_reduced_density_matrix", "hadamag_sre_even_sector", "hadamag_mana_qudit", "hadamag_mana_grad",
-    "hadamag_mana_mixed_qudit",
+    "hadamag_mana_mixed_qudit", "hadamag_reduced_density_matrix_qudit",
 ]
 
 
@@ -80,6 +80,7 @@ def load(path: str | None = None):
             "hadamag_mana_qudit": [V, V, I, I, I, PD, PD, V],
             "hadamag_mana_grad": [V, V, I, I, I, PD, V, V],
             "hadamag_mana_mixed_qudit": [V, V, I, I, I, PD, PD, V],
+            "hadamag_reduced_density_matrix_qudit": [V, V, I, I, I, ctypes.POINTER(I), I, V, V],
             "hadamag_mana_mixed": [V, V, I, I, PD, PD, V],
             "hadamag_reduced_density_matrix": [V, V, I, I, ctypes.POINTER(I), I, V, V],
         }

@@ -225,16 +225,20 @@ def mana_mixed(rho: torch.Tensor, d: int = 3):
     return m.value, list(sums)
 
 
-def reduced_density_matrix(psi: torch.Tensor, keep) -> torch.Tensor:
-    """rho_A = tr_B |psi><psi| of an N-qutrit state for the sites in `keep` (site keep[m] is digit
-    m of rho_A's row and column index); complex64 [3^k, 3^k] on the state's device."""
-    N = _check_state(psi, 3)
+def reduced_density_matrix(psi: torch.Tensor, keep, d: int = 3) -> torch.Tensor:
+    """rho_A = tr_B |psi><psi| of N sites of dimension d (qutrits by default) for the sites in
+    `keep` (site keep[m] is digit m of rho_A's row and column index); complex64 [d^k, d^k] on
+    the state's device."""
+    if int(d) < 2:
+        raise ValueError("d must be >= 2")
+    N = _check_state(psi, int(d))
     keep = [int(k) for k in keep]
     c = _ctx(psi)
-    rho = torch.empty((3 ** len(keep), 3 ** len(keep)), dtype=torch.complex64, device=psi.device)
+    rho = torch.empty((int(d) ** len(keep), int(d) ** len(keep)), dtype=torch.complex64, device=psi.device)
     arr = (ctypes.c_int * max(1, len(keep)))(*keep)
-    c.check(c.lib.hadamag_reduced_density_matrix(c.h, ctypes.c_void_p(psi.data_ptr()), N, _dtype_code(psi), arr,
-                                                 len(keep), ctypes.c_void_p(rho.data_ptr()), _stream(psi)),
+    c.check(c.lib.hadamag_reduced_density_matrix_qudit(c.h, ctypes.c_void_p(psi.data_ptr()), N, int(d),
+                                                       _dtype_code(psi), arr, len(keep),
+                                                       ctypes.c_void_p(rho.data_ptr()), _stream(psi)),
             "hadamag_reduced_density_matrix")
     return rho
 

@@ -1,7 +1,8 @@
-// rdm.cu -- reduced density matrix of a pure qutrit state, the partial trace that produces the
-// mixed states of the paper's mixed-state mana example (Sec. 3.3.3, Algorithm 6 input):
+// rdm.cu -- reduced density matrix of a pure state of qudits (qutrits by default), the partial
+// trace that produces the mixed states of the paper's mixed-state mana example (Sec. 3.3.3,
+// Algorithm 6 input):
 //     rho_A[r, c] = sum_x psi[(r, x)] conj(psi[(c, x)]),
-// r, c over the kept sites (site keep[m] = base-3 digit m of r and c), x over the traced-out
+// r, c over the kept sites (site keep[m] = base-d digit m of r and c), x over the traced-out
 // sites.  With A[r, x] = psi[off_keep[r] + off_rest[x]] (per-digit place values tabulated on the
 // host) this is the Gram product A A^dagger: a CTA computes a 16 x 16 tile of rho_A, staging
 // 16 x 32 gathered blocks of A for its rows and its columns in shared memory; each thread sums
@@ -56,15 +57,21 @@ __global__ void __launch_bounds__(256) rdm_kernel(const float2* __restrict__ psi
 
 using namespace hm;
 
-extern "C" hadamag_status hadamag_reduced_density_matrix(hadamag_ctx_t c, const void* psi, int N, hadamag_dtype dt,
-                                                         const int* keep, int n_keep, void* rho,
-                                                         hadamag_stream_t stream) {
+namespace {
+
+// Sites of dimension d: d^N <= 3^16 amplitudes, rho_A of side d^n_keep <= 3^10.
+hadamag_status rdm_run(hadamag_ctx_t c, const void* psi, int N, int d, hadamag_dtype dt, const int* keep,
+                       int n_keep, void* rho, hadamag_stream_t stream) {
     if (!c) return HADAMAG_ERR_INVALID_ARG;
     if (!aligned16(psi) || !keep || !rho || (reinterpret_cast<uintptr_t>(rho) & 7))
         return fail(c, HADAMAG_ERR_INVALID_ARG, "null or misaligned pointer");
-    if (N < 1 || N > 16) return fail(c, HADAMAG_ERR_INVALID_ARG, "N must be in [1, 16] (got %d)", N);
-    if (n_keep < 1 || n_keep > 10 || n_keep > N)
-        return fail(c, HADAMAG_ERR_INVALID_ARG, "need 1 <= n_keep <= min(N, 10) (got %d)", n_keep);
+    if (d < 2 || d > 13) return fail(c, HADAMAG_ERR_INVALID_ARG, "site dimension must be in [2, 13] (got %d)", d);
+    long long dimN = 1, dimA = 1;
+    for (int j = 0; j < N && dimN <= 43046721; ++j) dimN *= d;
+    for (int j = 0; j < n_keep && dimA <= 59049; ++j) dimA *= d;
+    if (N < 1 || dimN > 43046721) return fail(c, HADAMAG_ERR_INVALID_ARG, "need 1 <= N and d^N <= 3^16 (N = %d)", N);
+    if (n_keep < 1 || n_keep > N || dimA > 59049)
+        return fail(c, HADAMAG_ERR_INVALID_ARG, "need 1 <= n_keep <= N and d^n_keep <= 3^10 (got %d)", n_keep);
     if (dt != HADAMAG_C64 && dt != HADAMAG_C128) return fail(c, HADAMAG_ERR_INVALID_ARG, "bad dtype");
     std::vector<int> kept(N, 0);
     for (int m = 0; m < n_keep; ++m) {
@@ -73,18 +80,18 @@ extern "C" hadamag_status hadamag_reduced_density_matrix(hadamag_ctx_t c, const 
         kept[keep[m]] = 1;
     }
     std::vector<int64_t> place(N);
-    for (int j = 0, p = 1; j < N; ++j, p *= 3) place[j] = p;
+    for (int j = 0; j < N; ++j) place[j] = j ? place[j - 1] * d : 1;
     std::vector<int> rest;
     for (int j = 0; j < N; ++j)
         if (!kept[j]) rest.push_back(j);
-    // off(list)[i] = sum_m digit_m(i) * 3^(list[m])
+    // off(list)[i] = sum_m digit_m(i) * d^(list[m])  (digits in base d)
     auto offsets = [&](const int* sites, int n) {
         int64_t D = 1;
-        for (int m = 0; m < n; ++m) D *= 3;
+        for (int m = 0; m < n; ++m) D *= d;
         std::vector<int64_t> off((size_t)D);
         for (int64_t i = 0; i < D; ++i) {
             int64_t v = 0, q = i;
-            for (int m = 0; m < n; ++m, q /= 3) v += (q % 3) * place[sites[m]];
+            for (int m = 0; m < n; ++m, q /= d) v += (q % d) * place[sites[m]];
             off[(size_t)i] = v;
         }
         return off;
@@ -97,7 +104,7 @@ extern "C" hadamag_status hadamag_reduced_density_matrix(hadamag_ctx_t c, const 
     if (e != cudaSuccess) return cuda_fail(c, e, "cudaSetDevice");
     hadamag_status s;
     const float2* p;
-    if ((s = as_c64(c, psi, place[N - 1] * 3, dt, st, &p))) return s;
+    if ((s = as_c64(c, psi, (int64_t)dimN, dt, st, &p))) return s;
     if ((s = ensure_buf(c, c->rdm_idx, (size_t)(DA + DB) * sizeof(int64_t)))) return s;
     int64_t* dok = (int64_t*)c->rdm_idx.ptr;
     int64_t* dor = dok + DA;
@@ -109,4 +116,18 @@ extern "C" hadamag_status hadamag_reduced_density_matrix(hadamag_ctx_t c, const 
     c->launches++;
     if ((e = cudaGetLastError()) != cudaSuccess) return cuda_fail(c, e, "rdm_kernel");
     return HADAMAG_OK;
+}
+
+}  // namespace
+
+extern "C" hadamag_status hadamag_reduced_density_matrix(hadamag_ctx_t c, const void* psi, int N, hadamag_dtype dt,
+                                                         const int* keep, int n_keep, void* rho,
+                                                         hadamag_stream_t stream) {
+    return rdm_run(c, psi, N, 3, dt, keep, n_keep, rho, stream);
+}
+
+extern "C" hadamag_status hadamag_reduced_density_matrix_qudit(hadamag_ctx_t c, const void* psi, int N, int d,
+                                                               hadamag_dtype dt, const int* keep, int n_keep,
+                                                               void* rho, hadamag_stream_t stream) {
+    return rdm_run(c, psi, N, d, dt, keep, n_keep, rho, stream);
 }

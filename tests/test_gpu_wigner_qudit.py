@@ -160,3 +160,21 @@ def test_mixed_qudit_pure_and_maximally_mixed(d, N):
     D = d ** N
     mm, _ = hm.mana_mixed(on_dev(np.eye(D, dtype=np.complex64) / D), d)
     assert abs(mm) <= stab_tol(d, N)
+
+
+@pytest.mark.parametrize("d,N,keep", [(5, 3, [2, 0]), (7, 3, [1]), (5, 5, [4, 0, 2]), (2, 10, [9, 0, 3, 5])])
+def test_qudit_partial_trace_vs_oracle(d, N, keep):
+    from oracle import mixed
+    psi = I.gaussian_state(N, 4200 + d + N, d=d, dtype=np.complex64)
+    rho = hm.reduced_density_matrix(on_dev(psi), keep, d).cpu().numpy()
+    ro = mixed.reduced_density_matrix(psi, keep, d=d)
+    np.testing.assert_allclose(rho, ro, rtol=0, atol=2e-6 * np.abs(ro).max())
+
+
+def test_qudit_partial_trace_then_mana():
+    from oracle import mixed
+    d, N, keep = 5, 4, [3, 1]
+    psi = I.gaussian_state(N, 4300, d=d)
+    m, _ = hm.mana_mixed(hm.reduced_density_matrix(on_dev(psi), keep, d), d)
+    mo = Q.mana_mixed_fast(mixed.reduced_density_matrix(psi, keep, d=d), d)[0]
+    assert abs(m - mo) <= 1e-5 * max(1.0, abs(mo))  # rho rounded to complex64 on output

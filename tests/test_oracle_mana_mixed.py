@@ -165,3 +165,21 @@ def test_shift_gather_reproduces_algorithm_6(N):
     psi = I.gaussian_state(N, 330 + N, d=3)
     chi, _, _ = _shift_gather_chi(np.outer(psi, psi.conj()))
     assert np.log2(np.abs(chi.real).sum() / 3 ** N) == pytest.approx(oracle.mana(psi)[0], abs=1e-12)
+
+
+def test_reduced_density_matrix_of_qudits():
+    # d = 5: brute-force partial trace, and a product state's pure factor
+    d, N = 5, 3
+    psi = I.gaussian_state(N, 77, d=d)
+    rho = mixed.reduced_density_matrix(psi, [2, 0], d=d)
+    want = np.zeros((25, 25), dtype=np.complex128)
+    for z1 in range(d ** N):
+        for z2 in range(d ** N):
+            a = [(z1 // d ** k) % d for k in range(N)]
+            b = [(z2 // d ** k) % d for k in range(N)]
+            if a[1] == b[1]:
+                want[a[2] + d * a[0], b[2] + d * b[0]] += psi[z1] * np.conj(psi[z2])
+    np.testing.assert_allclose(rho, want, atol=1e-14)
+    f1, f2 = I.gaussian_state(1, 78, d=d), I.gaussian_state(2, 79, d=d)
+    np.testing.assert_allclose(mixed.reduced_density_matrix(np.kron(f2, f1), [1, 2], d=d),
+                               np.outer(f2, f2.conj()), atol=1e-14)
