@@ -70,3 +70,15 @@ def test_invalid_arguments():
     with pytest.raises(hm.HadamagError) as e:
         hm.sre_even_sector(psi, -1.0)
     assert e.value.code == 1
+
+
+@pytest.mark.parametrize("N", [1, 2, 3])
+def test_smallest_sizes(N):
+    # N = 1: the even sector is {a = 0} alone; N = 2: {0, 3}
+    for psi in (I.parity_state(N, 3710 + N, dtype=np.complex64),
+                I.parity_state(N, 3720 + N, parity=1, dtype=np.complex64)):
+        for n in (1.0, 2.0):
+            M, lost = hm.sre_even_sector(on_dev(psi), n)
+            Mo, losto = oracle.sre(psi, n)
+            assert abs(M - Mo) <= 1e-6 * max(1.0, abs(Mo)), (N, n, M, Mo)
+            assert abs(lost - losto) <= 2e-6
