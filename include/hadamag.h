@@ -63,6 +63,16 @@ hadamag_status hadamag_destroy(hadamag_ctx_t ctx);
 /* Choose the transform path for later calls on this context (default AUTO); INVALID_ARG
  * for a value outside the enum. */
 hadamag_status hadamag_set_path(hadamag_ctx_t ctx, hadamag_path path);
+/* Fast path for non-integer n (off by default): with on = 1 the CUDA-core exact-SRE kernels
+ * form |c|^{2n} as exp2f(n log2f(.)) in FP32 (summed in FP32 per thread, FP64 across threads)
+ * instead of FP64 powers, where n <= 4 and n (N + 2) <= 100 (the values stay in FP32's normal
+ * range for normalised states); elsewhere, and on the tensor path, FP64 powers are kept.  Error:
+ * with log2f (1 ulp) and exp2f (2 ulp), and the FP32 rounding of n and of the product, a term
+ * |c|^{2n} carries a relative error below (2 + 2 ln2 n |log2 |c|^2|) 2^-23, about
+ * (2 + 2 ln2 n N) 2^-23 for the terms of typical size 2^-N that dominate the sum, so
+ * |dM_n| <~ (2 + 2 ln2 n N) 2^-23 / (ln2 |1 - n|) beyond the FP32 transform's own error.
+ * INVALID_ARG for a value other than 0 or 1. */
+hadamag_status hadamag_set_fp32_powers(hadamag_ctx_t ctx, int on);
 /* Bound of every inter-CTA wait, in polling iterations (~0.1 us each; default 2^25), and a
  * value added to every wait target.  A non-zero bias makes waits unsatisfiable; it exists
  * only so tests can check that a wait that runs out returns HADAMAG_ERR_TIMEOUT. */

@@ -26,7 +26,7 @@ EXPORTS = [
     "hadamag_mana", "hadamag_mana_sums", "hadamag_sre_grad", "hadamag_sre_batched",
     "hadamag_sre_noalloc", "hadamag_batched_status", "hadamag_sre_ti", "hadamag_mana_mixed",
     "hadamag_reduced_density_matrix", "hadamag_sre_even_sector", "hadamag_mana_qudit", "hadamag_mana_grad",
-    "hadamag_mana_mixed_qudit", "hadamag_reduced_density_matrix_qudit",
+    "hadamag_mana_mixed_qudit", "hadamag_reduced_density_matrix_qudit", "hadamag_set_fp32_powers",
 ]
 
 
@@ -61,6 +61,7 @@ def load(path: str | None = None):
             "hadamag_destroy": [V],
             "hadamag_set_path": [V, I],
             "hadamag_set_wait_limit": [V, ctypes.c_longlong, ctypes.c_uint],
+            "hadamag_set_fp32_powers": [V, I],
             "hadamag_launch_count": [V, ctypes.POINTER(U64)],
             "hadamag_status_string": [I],
             "hadamag_last_error": [V],
@@ -128,6 +129,10 @@ class Context:
     def set_path(self, path: int):
         self.check(self.lib.hadamag_set_path(self.h, int(path)), "hadamag_set_path")
         self.path = int(path)
+
+    def set_fp32_powers(self, on: bool):
+        """Opt into FP32 powers for non-integer n (see hadamag_set_fp32_powers)."""
+        self.check(self.lib.hadamag_set_fp32_powers(self.h, 1 if on else 0), "hadamag_set_fp32_powers")
 
     def set_wait_limit(self, spins: int, bias: int = 0):
         self.check(self.lib.hadamag_set_wait_limit(self.h, int(spins), int(bias)), "hadamag_set_wait_limit")

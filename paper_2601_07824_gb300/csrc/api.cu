@@ -114,7 +114,8 @@ TwoPlan plan_twopass(int N) {
 // per-X-string triples are written to terms (device).
 hadamag_status run_sre(hadamag_ctx_t c, const float2* psi, int N, double n, int64_t count,
                        const int64_t* a_list, int per_a, double* terms, cudaStream_t st, int64_t* nparts) {
-    const int mode = sre_mode(n);
+    int mode = sre_mode(n);
+    if (mode == 0 && c->fp32_powers && n <= 4.0 && n * (N + 2) <= 100.0) mode = 4;
     hadamag_status s;
     cudaError_t e;
     if (N <= 15) {
@@ -252,6 +253,12 @@ extern "C" hadamag_status hadamag_set_path(hadamag_ctx_t c, hadamag_path p) {
     if (!c || (p != HADAMAG_PATH_AUTO && p != HADAMAG_PATH_CUDACORE && p != HADAMAG_PATH_TENSOR))
         return HADAMAG_ERR_INVALID_ARG;
     c->path = p;
+    return HADAMAG_OK;
+}
+
+extern "C" hadamag_status hadamag_set_fp32_powers(hadamag_ctx_t c, int on) {
+    if (!c || (on != 0 && on != 1)) return HADAMAG_ERR_INVALID_ARG;
+    c->fp32_powers = on;
     return HADAMAG_OK;
 }
 

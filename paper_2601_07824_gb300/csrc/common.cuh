@@ -158,6 +158,12 @@ struct Acc {
         s1 += sq.x + sq.y;
         if constexpr (MODE == 1) {
             u += (sq.x > 0.f ? sq.x * log2f(sq.x) : 0.f) + (sq.y > 0.f ? sq.y * log2f(sq.y) : 0.f);
+        } else if constexpr (MODE == 4) {
+            // FP32 powers (opt-in fast path for non-integer n): sq^n = exp2(n log2 sq), the 4^n of
+            // the half-length form applied in finish3; callers keep n (N + 2) <= 100 so that the
+            // values stay in FP32's normal range
+            const float nf = (float)nq;
+            q += (sq.x > 0.f ? exp2f(nf * log2f(sq.x)) : 0.f) + (sq.y > 0.f ? exp2f(nf * log2f(sq.y)) : 0.f);
         } else {
             double px = 4.0 * (double)sq.x, py = 4.0 * (double)sq.y;
             qd += (px > 0.0 ? exp2(nq * log2(px)) : 0.0) + (py > 0.0 ? exp2(nq * log2(py)) : 0.0);
@@ -193,6 +199,7 @@ __device__ __forceinline__ void finish3(float q, float s1, float u, double qd, d
     if constexpr (MODE == 2) out[0] = 16.0 * (double)q;
     else if constexpr (MODE == 3) out[0] = 64.0 * (double)q;
     else if constexpr (MODE == 1) out[0] = S1;
+    else if constexpr (MODE == 4) out[0] = exp2(2.0 * nq) * (double)q;
     else out[0] = qd;
     // sum 4x^2 log2(4x^2) = 4 (2 sum x^2 + sum x^2 log2 x^2)
     out[2] = (MODE == 1) ? 4.0 * (2.0 * (double)s1 + (double)u) : 0.0;

@@ -35,6 +35,7 @@ struct hadamag_ctx_s {
     long long spin_limit = 1ll << 25;
     unsigned wait_bias = 0;
     int autotune = 1;
+    int fp32_powers = 0;  // non-integer n: FP32 powers (mode 4) where n <= 4 and n (N + 2) <= 100
     void* host_table = nullptr;  // pinned copy of the batched state table
     size_t host_table_bytes = 0;
     uint64_t launches = 0;

@@ -54,6 +54,7 @@ cudaError_t launch_onepass(OnepassArgs& A, int mode, int sm_count, cudaStream_t 
         case 1: return sre_fwd_onepass_n1(A, sm_count, st);
         case 2: return sre_fwd_onepass_n2(A, sm_count, st);
         case 3: return sre_fwd_onepass_n3(A, sm_count, st);
+        case 4: return sre_fwd_onepass_n4(A, sm_count, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -72,6 +73,7 @@ cudaError_t launch_twopass(const TwoPassParams& P, int mode, int grid, cudaStrea
         case 1: return sre_fwd_twopass_n1(P, grid, st);
         case 2: return sre_fwd_twopass_n2(P, grid, st);
         case 3: return sre_fwd_twopass_n3(P, grid, st);
+        case 4: return sre_fwd_twopass_n4(P, grid, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -84,6 +86,7 @@ cudaError_t twopass_max_grid(int N, int mode, int sm_count, int* grid) {
         case 1: e = sre_fwd_twopass_occ_n1(N, &occ); break;
         case 2: e = sre_fwd_twopass_occ_n2(N, &occ); break;
         case 3: e = sre_fwd_twopass_occ_n3(N, &occ); break;
+        case 4: e = sre_fwd_twopass_occ_n4(N, &occ); break;
         default: return cudaErrorInvalidValue;
     }
     if (e != cudaSuccess) return e;

@@ -368,19 +368,23 @@ static cudaError_t twopass_occ_m(int N, int* occ) {
     HM_TWOPASS_SWITCH(N, return (twopass_prepare<KK, MM, MODE>(occ)))
 }
 
-// Per-mode entry points (MODE 0: any n, 1: n = 1, 2: n = 2, 3: n = 3), one translation unit each.
+// Per-mode entry points (MODE 0: any n with FP64 powers, 1: n = 1, 2: n = 2, 3: n = 3, 4: any n
+// with FP32 powers), one translation unit each.
 cudaError_t sre_fwd_onepass_n0(OnepassArgs& A, int sm_count, cudaStream_t st);
 cudaError_t sre_fwd_onepass_n1(OnepassArgs& A, int sm_count, cudaStream_t st);
 cudaError_t sre_fwd_onepass_n2(OnepassArgs& A, int sm_count, cudaStream_t st);
 cudaError_t sre_fwd_onepass_n3(OnepassArgs& A, int sm_count, cudaStream_t st);
+cudaError_t sre_fwd_onepass_n4(OnepassArgs& A, int sm_count, cudaStream_t st);
 cudaError_t sre_fwd_twopass_n0(const TwoPassParams& P, int grid, cudaStream_t st);
 cudaError_t sre_fwd_twopass_n1(const TwoPassParams& P, int grid, cudaStream_t st);
 cudaError_t sre_fwd_twopass_n2(const TwoPassParams& P, int grid, cudaStream_t st);
 cudaError_t sre_fwd_twopass_n3(const TwoPassParams& P, int grid, cudaStream_t st);
+cudaError_t sre_fwd_twopass_n4(const TwoPassParams& P, int grid, cudaStream_t st);
 cudaError_t sre_fwd_twopass_occ_n0(int N, int* occ);
 cudaError_t sre_fwd_twopass_occ_n1(int N, int* occ);
 cudaError_t sre_fwd_twopass_occ_n2(int N, int* occ);
 cudaError_t sre_fwd_twopass_occ_n3(int N, int* occ);
+cudaError_t sre_fwd_twopass_occ_n4(int N, int* occ);
 
 #define HM_SRE_FWD_MODE(M_)                                                                      \
     cudaError_t sre_fwd_onepass_n##M_(OnepassArgs& A, int sm_count, cudaStream_t st) {          \
