@@ -120,9 +120,17 @@ def _transform_rows(V: np.ndarray, d: int, N: int) -> np.ndarray:
 
 
 def _shift_indices(dig: np.ndarray, da: np.ndarray, d: int, pw: np.ndarray):
-    """idx(x - a) and idx(-x - a) (digit-wise mod d) for the shifts in da and every x."""
-    i1 = (((dig[None, :, :] - da[:, None, :]) % d) * pw).sum(-1)
-    i2 = (((-dig[None, :, :] - da[:, None, :]) % d) * pw).sum(-1)
+    """idx(x - a) and idx(-x - a) (digit-wise mod d) for the shifts in da and every x, summed
+    site by site from (d x d) tables of ((x_k -+ a_k) mod d) d^k."""
+    r = np.arange(d)
+    sub = (r[None, :] - r[:, None]) % d   # [a_k, x_k] -> (x_k - a_k) mod d
+    neg = (-r[None, :] - r[:, None]) % d  # [a_k, x_k] -> (-x_k - a_k) mod d
+    i1 = np.zeros((da.shape[0], dig.shape[0]), dtype=np.int64)
+    i2 = np.zeros_like(i1)
+    for k in range(dig.shape[1]):
+        ia, ix = da[:, k][:, None], dig[None, :, k]
+        i1 += (sub * pw[k])[ia, ix]
+        i2 += (neg * pw[k])[ia, ix]
     return i1, i2
 
 
