@@ -70,3 +70,20 @@ def test_stabilizer_generators():
 def test_interleaved_layout():
     psi = np.array([1 + 2j, 3 - 4j], dtype=np.complex128)
     np.testing.assert_array_equal(I.to_interleaved(psi), np.array([1, 2, 3, -4], dtype=np.float32))
+
+
+def test_symmetric_state_generators():
+    # U(1): support on Hamming weight k only; Z_2: support on one weight parity only
+    for N, k in ((6, 3), (7, 2), (1, 1)):
+        u = I.u1_state(N, k, 9)
+        w = np.array([bin(z).count("1") for z in range(2 ** N)])
+        assert np.linalg.norm(u) == pytest.approx(1.0, abs=1e-12)
+        assert np.all(u[w != k] == 0) and np.count_nonzero(u[w == k]) == int((w == k).sum())
+        np.testing.assert_array_equal(u, I.u1_state(N, k, 9))
+        assert not np.allclose(u, I.u1_state(N, k, 10))
+    for N, par in ((5, 0), (5, 1), (1, 0)):
+        p = I.parity_state(N, 11, parity=par)
+        w = np.array([bin(z).count("1") for z in range(2 ** N)])
+        assert np.linalg.norm(p) == pytest.approx(1.0, abs=1e-12)
+        assert np.all(p[(w & 1) != par] == 0)
+    assert I.u1_state(8, 4, 1, dtype=np.complex64).dtype == np.complex64
