@@ -44,7 +44,9 @@ def parse():
                     help="also time N=22, mana N=11, MC N=28, batched, thermodynamic integration N=20, "
                          "mixed-state mana N=8, even-sector SRE N=20, qudit mana d=5, mana gradient")
     ap.add_argument("--only", default="",
-                    help="profiling aid: run just the named --extra workload (e.g. ti_N20_L10) and print it")
+                    help="run just the named --extra workloads (comma-separated, e.g. ti_N20_L10) and print them")
+    ap.add_argument("--no-new-rows", action="store_true",
+                    help="skip the separate-process timing of the Algorithm 3 / 6, sector and qudit workloads")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--xstrings", type=int, default=0,
                     help="profiling aid: each step evaluates only the first K X-strings of the "
@@ -263,6 +265,14 @@ def main():
     import paper_2601_07824_gb300 as hm
     from paper_2601_07824_gb300 import _lib
 
+    if args.only:
+        if rank == 0:
+            sms = torch.cuda.get_device_properties(dev).multi_processor_count
+            print(json.dumps({"extra": extra_workloads(hm, dev, sms, args.only)}), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+
     N = args.N
     psi_np, desc = workload_state(N)
     psi = torch.from_numpy(psi_np).to(dev)
@@ -277,13 +287,6 @@ def main():
         if world > 1:
             dist.barrier()
         torch.cuda.synchronize(dev)
-
-    if args.only:
-        if rank == 0:
-            print(json.dumps({"extra": extra_workloads(hm, dev, sm_count, args.only)}), flush=True)
-        if world > 1:
-            dist.destroy_process_group()
-        return
 
     M = ln = None
     if args.xstrings > 0:
@@ -373,10 +376,32 @@ def main():
         line["cpu_baseline"] = cb
     if rank == 0 and args.extra:
         line["extra"] = extra_workloads(hm, dev, sm_count)
+    if rank == 0 and world == 1 and not args.no_new_rows:
+        line["new_rows"] = new_rows_in_child()
     if rank == 0:
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+NEW_ROWS = ("ti_N20_L10", "mana_mixed_N8_of_10", "sre_even_sector_N20_u1", "mana_qudit_d5_N6", "mana_grad_d3_N9")
+
+
+def new_rows_in_child(timeout_s: float = 300.0):
+    """Times the Algorithm 3 / Algorithm 6, even-sector, qudit and mana-gradient workloads (the
+    --extra lines of those rows) in a separate process, after the headline measurement: a CUDA
+    error there cannot reach the headline's context, and a time limit bounds it."""
+    cmd = [sys.executable, os.path.abspath(__file__), "--only", ",".join(NEW_ROWS)]
+    try:
+        r = subprocess.run(cmd, capture_output=True, text=True, timeout=timeout_s)
+    except subprocess.TimeoutExpired:
+        return {"error": f"timed out after {timeout_s:.0f} s"}
+    for ln in reversed(r.stdout.strip().splitlines()):
+        try:
+            return json.loads(ln)["extra"]
+        except (ValueError, KeyError):
+            continue
+    return {"error": f"exit {r.returncode}: " + (r.stderr.strip().splitlines() or [""])[-1][:200]}
 
 
 def extra_workloads(hm, dev, sm_count, only: str = ""):
@@ -397,8 +422,10 @@ def extra_workloads(hm, dev, sm_count, only: str = ""):
         torch.cuda.synchronize(dev)
         return (time.perf_counter() - t0) / reps, r
 
+    wanted = set(only.split(",")) if only else None
+
     def guard(key, fn):
-        if only and key != only:
+        if wanted is not None and key not in wanted:
             return
         try:
             out[key] = fn()
@@ -409,7 +436,7 @@ def extra_workloads(hm, dev, sm_count, only: str = ""):
 
     # exact M2 at N = 22 (Gaussian state): FP32 CUDA-core path vs tensor-core path
     psi22 = torch.from_numpy(inputs.gaussian_state(22, 2201, dtype=np.complex64)).to(dev) \
-        if not only or only.startswith("sre_N22") else None
+        if wanted is None or wanted & {"sre_N22_cudacore", "sre_N22_tensor"} else None
     res = {}
     for name, p in (("cudacore", _lib.PATH_CUDACORE), ("tensor", _lib.PATH_TENSOR)):
         def run22(p=p, name=name):

@@ -97,3 +97,15 @@ def test_multi_rank_timing_takes_the_slowest_rank():
     for rank, t_max, rate in res:
         assert t_max == 2.5  # every rank sees the slowest rank's time
         assert rate == pytest.approx(2 * 3 * 2.0 ** 20 / 2.5)  # whole-job aggregate (weak scaling)
+
+
+def test_new_rows_child_reports_failures_without_raising():
+    # the default run times the newer workloads in a child process; a child that fails (here:
+    # no GPU) or overruns its limit must give an error entry, never an exception
+    import bench
+    out = bench.new_rows_in_child(timeout_s=0.001)
+    assert "error" in out and "timed out" in out["error"]
+    import torch
+    if not torch.cuda.is_available():
+        out = bench.new_rows_in_child(timeout_s=300)
+        assert isinstance(out, dict) and "error" in out
