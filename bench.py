@@ -486,7 +486,9 @@ def extra_workloads(hm, dev, sm_count, only: str = ""):
         L, n_s, burn = 10, 2000, 200
         dt, r = timed(lambda: hm.sre_ti(psi, L, n_s, 2002, burn_in=burn), warm=False)
         evals = L * (n_s + burn + 1)
-        return {"strings_per_s": evals * 2.0 ** 20 / dt, "evaluations_per_s": evals / dt,
+        rate = evals * 2.0 ** 20 / dt
+        return {"strings_per_s": rate, "alu_frac": ops_per_string(20) * rate / fp32_peak_ops(sm_count, 2070.0),
+                "evaluations_per_s": evals / dt,
                 "steps_per_s": (n_s + burn) / dt, "s": dt, "M2": r[0], "dM2": r[1], "L": L, "n_s": n_s,
                 "burn_in": burn}
     guard("ti_N20_L10", ti20)
@@ -500,7 +502,9 @@ def extra_workloads(hm, dev, sm_count, only: str = ""):
         t_rdm, rho = timed(lambda: hm.reduced_density_matrix(psi, keep), reps=3)
         dt, r = timed(lambda: hm.mana_mixed(rho), reps=3)
         pts = 9.0 ** 8
+        hbm, hsrc = measured_peak("hbm_gbs", 6800.0)
         return {"points_per_s": pts / dt, "s": dt, "mana": r[0], "rho_read_GBps": pts * 8 / dt / 1e9,
+                "hbm_frac": pts * 8 / dt / 1e9 / hbm, "peak_source": hsrc,
                 "rdm_s": t_rdm, "rdm_tflops": 8.0 * 9.0 ** 8 * 3.0 ** 2 / t_rdm / 1e12}
     guard("mana_mixed_N8_of_10", mixed8)
 
@@ -510,20 +514,25 @@ def extra_workloads(hm, dev, sm_count, only: str = ""):
         t_full, rf = timed(lambda: hm.sre(psi, 2.0))
         t_even, re_ = timed(lambda: hm.sre_even_sector(psi, 2.0))
         return {"full_s": t_full, "even_s": t_even, "speedup": t_full / t_even, "M2_full": rf[0], "M2_even": re_[0],
-                "even_strings_per_s": 2.0 ** 39 / t_even}
+                "even_strings_per_s": 2.0 ** 39 / t_even,
+                "alu_frac": ops_per_string(20) * 2.0 ** 39 / t_even / fp32_peak_ops(sm_count, 2070.0)}
     guard("sre_even_sector_N20_u1", even20)
 
     # odd-prime qudits: mana at d = 5, N = 6, and the qutrit mana gradient at N = 9
     def qudit5():
         psi = torch.from_numpy(inputs.gaussian_state(6, 501, d=5, dtype=np.complex64)).to(dev)
         dt, r = timed(lambda: hm.mana_qudit(psi, 5), reps=3)
-        return {"points_per_s": 25.0 ** 6 / dt, "s": dt, "mana": r[0]}
+        # N d complex multiply-adds (4 FMAs) per point in the direct d-point sums
+        return {"points_per_s": 25.0 ** 6 / dt, "s": dt, "mana": r[0],
+                "alu_frac": 4 * 6 * 5 * 25.0 ** 6 / dt / fp32_peak_ops(sm_count, 2070.0)}
     guard("mana_qudit_d5_N6", qudit5)
 
     def grad3():
         psi = torch.from_numpy(inputs.gaussian_state(9, 901, d=3, dtype=np.complex64)).to(dev)
         dt, r = timed(lambda: hm.mana_grad(psi, 3), reps=3)
-        return {"points_per_s": 9.0 ** 9 / dt, "s": dt, "mana": r[0]}
+        # two transforms of N d complex multiply-adds (4 FMAs each) per point
+        return {"points_per_s": 9.0 ** 9 / dt, "s": dt, "mana": r[0],
+                "alu_frac": 2 * 4 * 9 * 3 * 9.0 ** 9 / dt / fp32_peak_ops(sm_count, 2070.0)}
     guard("mana_grad_d3_N9", grad3)
     return out
 
