@@ -4,9 +4,11 @@
  * (arXiv 2601.07824).
  *
  * Conventions shared by every call
- *   - A qubit state has 2^N amplitudes, a qutrit state 3^N; site j is digit j of the index
- *     (least significant first).  Amplitudes are interleaved (re, im): HADAMAG_C64 = two
- *     floats, HADAMAG_C128 = two doubles.  Device pointers must be 16-byte aligned.
+ *   - A state of N sites of dimension d has d^N amplitudes (qubits d = 2, qutrits d = 3,
+ *     qudits of odd prime d); site j is base-d digit j of the index (least significant
+ *     first).  A density matrix is d^N x d^N, row-major.  Amplitudes are interleaved (re, im):
+ *     HADAMAG_C64 = two floats, HADAMAG_C128 = two doubles.  Device pointers must be 16-byte
+ *     aligned (8-byte where a call says so).
  *   - States are NOT renormalised: every quantity is the paper's formula evaluated on the
  *     vector as given; lost_norm reports 1 - sum_P <P>^2 / 2^N (Sec. 4.1).
  *   - Ownership: every pointer belongs to the caller; the library never frees or keeps it
