@@ -168,7 +168,7 @@ def test_odd_sectors_vanish_and_even_sector_sre_is_exact(label, psi):
     Sq, S1, _ = oracle.sre_terms(psi, 2.0)
     odd = ~ti.even_mask(N)
     assert np.abs(Sq[odd]).max() < 1e-14 and np.abs(S1[odd]).max() < 1e-14
-    for q in (1.0, 2.0, 3.0):
+    for q in (0.5, 1.0, 2.0, 2.5, 3.0):
         M, lost = oracle.sre(psi, q)
         Me, loste = oracle.sre_even_sector(psi, q)
         assert Me == pytest.approx(M, abs=1e-11), q
