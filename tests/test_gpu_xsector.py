@@ -34,8 +34,9 @@ def on_dev(a):
     ("z2_N16", I.parity_state(16, 3704, dtype=np.complex64)),
 ])
 def test_even_sector_equals_full_sre_on_symmetric_states(label, psi):
-    # every n up to 13 qubits; n = 2 at 16, where each FP64 oracle call costs seconds
-    for n in ((1.0, 2.0, 3.0) if psi.size <= 2 ** 13 else (2.0,)):
+    # n = 0.5 ... 3 up to 13 qubits (FP64 powers for the non-integer ones); n = 2 at 16, where
+    # each FP64 oracle call costs seconds
+    for n in ((0.5, 1.0, 2.0, 2.5, 3.0) if psi.size <= 2 ** 13 else (2.0,)):
         M, lost = hm.sre_even_sector(on_dev(psi), n)
         Mo, losto = oracle.sre(psi, n)
         assert abs(M - Mo) <= 1e-6 * max(1.0, abs(Mo)), (label, n, M, Mo)
