@@ -19,7 +19,7 @@
 
 namespace hm {
 
-constexpr int QUDIT_MAXN = 8;
+constexpr int QUDIT_MAXN = 9;  // d = 3: 3^9 = 19683 <= QUDIT_MAXDIM
 constexpr int QUDIT_MAXDIM = 25600;
 
 // idx(x - a) and idx(-x - a), digit-wise mod D (ad: the digits of a)
