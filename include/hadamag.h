@@ -292,6 +292,52 @@ hadamag_status hadamag_sre_grad(hadamag_ctx_t ctx, const void* psi_dev, int N, h
                                 double* M2_out, void* grad_dev, hadamag_stream_t stream);
 
 /*
+ * One state's computation split by X-string, for several GPUs or several calls.  The a-loop of
+ * Algorithm 2 is a sum of independent per-X-string terms, which Sec. 4.1 distributes over
+ * threads, processes and GPUs, combining their partial sums with one reduction.
+ *
+ * hadamag_sre_chunk(N): the chunk size, 2^min(N, 12) X-strings (0 for N outside [1, 24]).
+ * Every slice starts and ends on a multiple of it.
+ *
+ * hadamag_sre_slice: the sums of Eq. (sre) over the X-strings a0 <= a < a1, one triple
+ * [sum |c|^{2n}, sum |c|^2, sum |c|^2 log2 |c|^2 (n = 1, else 0)] per chunk of consecutive
+ * X-strings, written to chunks_dev ((a1 - a0) / chunk * 3 doubles on the device, 8-byte
+ * aligned), chunk k of the slice holding the X-strings a0 + k chunk .. a0 + (k + 1) chunk - 1.
+ * A chunk's triple is a fixed-order FP64 sum that depends only on the chunk, so every
+ * chunk-aligned partition of [0, 2^N) yields the same triples bit for bit, on any GPU.
+ * Same N, n, dtype and path rules as hadamag_sre; a0, a1 multiples of the chunk size with
+ * 0 <= a0 <= a1 <= 2^N (else INVALID_ARG).  Synchronises `stream` to read the status word.
+ *
+ * hadamag_sre_combine (host only, no CUDA call): adds the 2^N / chunk triples of all slices in
+ * chunk order (chunks_host, host memory, gathered from every slice) and returns M_n and
+ * lost_norm as hadamag_sre does.  INVALID_ARG if nchunks is not 2^N / chunk.
+ */
+int64_t hadamag_sre_chunk(int N);
+hadamag_status hadamag_sre_slice(hadamag_ctx_t ctx, const void* psi_dev, int N, double n,
+                                 hadamag_dtype dtype, int64_t a0, int64_t a1, double* chunks_dev,
+                                 hadamag_stream_t stream);
+hadamag_status hadamag_sre_combine(int N, double n, const double* chunks_host, int64_t nchunks,
+                                   double* M_out, double* lost_norm_out);
+
+/*
+ * The adjoint of hadamag_sre_grad split by X-string in the same way.
+ * hadamag_sre_grad_slice: the part of dS_2/dpsi* contributed by the X-strings a0 <= a < a1
+ * (unscaled; the sum over a of the adjoint formula above restricted to the slice) into dS_dev
+ * (2^N complex128 on the device, overwritten), and sums_out[0] = that slice's part of S_2,
+ * sums_out[1] = its part of sum |c|^2 (host doubles).  1 <= N <= 20; a0, a1 multiples of
+ * hadamag_sre_chunk(N).  Synchronises `stream`.
+ * hadamag_sre_grad_combine: from the dS_2/dpsi* and S_2 summed over all slices (e.g. by an
+ * all-reduce), grad_dev = -dS / (ln 2 S_2) (2^N amplitudes of `dtype` on the device) and
+ * M2_out = -log2(S_2 / 2^N) (host).  S_2 must be finite and > 0.  Synchronises `stream`.
+ */
+hadamag_status hadamag_sre_grad_slice(hadamag_ctx_t ctx, const void* psi_dev, int N, hadamag_dtype dtype,
+                                      int64_t a0, int64_t a1, double* sums_out, void* dS_dev,
+                                      hadamag_stream_t stream);
+hadamag_status hadamag_sre_grad_combine(hadamag_ctx_t ctx, const void* dS_dev, int N, double S2,
+                                        hadamag_dtype dtype, double* M2_out, void* grad_dev,
+                                        hadamag_stream_t stream);
+
+/*
  * Many states of uneven N (10 <= N_i <= 18, complex64) in ONE persistent launch (the batched
  * form for many states of uneven N; not in the paper): M_2 of state i into M2_dev[i] (device doubles) and, if
  * want_grad, dM_2/dpsi* into grad_dev[i] (complex64).  psi_dev and grad_dev are HOST arrays of

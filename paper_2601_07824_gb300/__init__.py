@@ -16,6 +16,7 @@ from __future__ import annotations
 
 __all__ = ["sre", "sre_host", "sre_terms", "sre_even_sector", "mc_xstrings", "sre_mc", "sre_ti", "mana",
            "mana_sums", "mana_qudit", "mana_grad", "mana_mixed", "reduced_density_matrix", "sre_grad",
+           "sre_chunk", "sre_slice", "sre_combine", "sre_grad_slice", "sre_grad_combine",
            "SREFunction",
            "sre_batched",
            "context", "HadamagError", "PATH_AUTO", "PATH_CUDACORE", "PATH_TENSOR"]

@@ -27,6 +27,8 @@ EXPORTS = [
     "hadamag_sre_noalloc", "hadamag_batched_status", "hadamag_sre_ti", "hadamag_mana_mixed",
     "hadamag_reduced_density_matrix", "hadamag_sre_even_sector", "hadamag_mana_qudit", "hadamag_mana_grad",
     "hadamag_mana_mixed_qudit", "hadamag_reduced_density_matrix_qudit", "hadamag_set_fp32_powers",
+    "hadamag_sre_chunk", "hadamag_sre_slice", "hadamag_sre_combine", "hadamag_sre_grad_slice",
+    "hadamag_sre_grad_combine",
 ]
 
 
@@ -84,11 +86,21 @@ def load(path: str | None = None):
             "hadamag_reduced_density_matrix_qudit": [V, V, I, I, I, ctypes.POINTER(I), I, V, V],
             "hadamag_mana_mixed": [V, V, I, I, PD, PD, V],
             "hadamag_reduced_density_matrix": [V, V, I, I, ctypes.POINTER(I), I, V, V],
+            "hadamag_sre_chunk": [I],
+            "hadamag_sre_slice": [V, V, I, D, I, L, L, V, V],
+            "hadamag_sre_combine": [I, D, PD, L, PD, PD],
+            "hadamag_sre_grad_slice": [V, V, I, I, L, L, PD, V, V],
+            "hadamag_sre_grad_combine": [V, V, I, D, I, PD, V, V],
         }
         for name, args in sig.items():
             f = getattr(lib, name)
             f.argtypes = args
-            f.restype = ctypes.c_char_p if name in ("hadamag_status_string", "hadamag_last_error") else I
+            if name in ("hadamag_status_string", "hadamag_last_error"):
+                f.restype = ctypes.c_char_p
+            elif name == "hadamag_sre_chunk":
+                f.restype = L
+            else:
+                f.restype = I
         _lib = lib
         return lib
 

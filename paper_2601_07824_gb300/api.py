@@ -14,6 +14,7 @@ import torch
 from ._lib import (C64, C128, PATH_AUTO, PATH_CUDACORE, PATH_TENSOR, HadamagError, context)
 
 __all__ = ["sre", "sre_host", "sre_terms", "mc_xstrings", "sre_mc", "mana", "mana_sums", "sre_grad",
+           "sre_chunk", "sre_slice", "sre_combine", "sre_grad_slice", "sre_grad_combine",
            "SREFunction", "sre_batched", "context", "HadamagError", "PATH_AUTO",
            "PATH_CUDACORE", "PATH_TENSOR"]
 
@@ -262,6 +263,69 @@ def sre_grad(psi: torch.Tensor):
     c.check(c.lib.hadamag_sre_grad(c.h, ctypes.c_void_p(psi.data_ptr()), N, _dtype_code(psi),
                                    ctypes.byref(M), ctypes.c_void_p(g.data_ptr()), _stream(psi)),
             "hadamag_sre_grad")
+    return M.value, g
+
+
+def sre_chunk(N: int) -> int:
+    """Chunk size of the X-string slices (slices start and end on multiples of it)."""
+    from ._lib import load
+    ch = int(load().hadamag_sre_chunk(int(N)))
+    if ch <= 0:
+        raise ValueError(f"N = {N} outside the exact-SRE range")
+    return ch
+
+
+def sre_slice(psi: torch.Tensor, n: float, a0: int, a1: int, path: int | None = None) -> torch.Tensor:
+    """Per-chunk sums [sum |c|^{2n}, sum |c|^2, sum |c|^2 log2 |c|^2] over the X-strings
+    a0 <= a < a1, as a float64 tensor [(a1 - a0) / chunk, 3] on the state's device."""
+    N = _check_state(psi)
+    ch = sre_chunk(N)
+    out = torch.empty((max(0, (int(a1) - int(a0)) // ch), 3), dtype=torch.float64, device=psi.device)
+    c = _ctx(psi)
+    buf = out if out.numel() else torch.empty(3, dtype=torch.float64, device=psi.device)
+    with _path(c, path):
+        c.check(c.lib.hadamag_sre_slice(c.h, ctypes.c_void_p(psi.data_ptr()), N, float(n), _dtype_code(psi),
+                                        int(a0), int(a1), ctypes.c_void_p(buf.data_ptr()), _stream(psi)),
+                "hadamag_sre_slice")
+    return out
+
+
+def sre_combine(N: int, n: float, chunks) -> tuple:
+    """(M_n, lost_norm) from the chunk sums of every slice, in chunk order (host only)."""
+    from ._lib import load
+    a = np.ascontiguousarray(np.asarray(chunks.cpu() if isinstance(chunks, torch.Tensor) else chunks,
+                                        dtype=np.float64)).reshape(-1, 3)
+    M, ln = ctypes.c_double(), ctypes.c_double()
+    rc = load().hadamag_sre_combine(int(N), float(n), a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)),
+                                    a.shape[0], ctypes.byref(M), ctypes.byref(ln))
+    if rc != 0:
+        raise HadamagError(rc, "hadamag_sre_combine")
+    return M.value, ln.value
+
+
+def sre_grad_slice(psi: torch.Tensor, a0: int, a1: int):
+    """((S_2, S_1) of the slice, dS_2/dpsi* of the slice as complex128 [2^N] on the device)."""
+    N = _check_state(psi)
+    dS = torch.empty(psi.numel(), dtype=torch.complex128, device=psi.device)
+    sums = (ctypes.c_double * 2)()
+    c = _ctx(psi)
+    c.check(c.lib.hadamag_sre_grad_slice(c.h, ctypes.c_void_p(psi.data_ptr()), N, _dtype_code(psi), int(a0),
+                                         int(a1), sums, ctypes.c_void_p(dS.data_ptr()), _stream(psi)),
+            "hadamag_sre_grad_slice")
+    return (sums[0], sums[1]), dS
+
+
+def sre_grad_combine(dS: torch.Tensor, S2: float, dtype=torch.complex64):
+    """(M_2, dM_2/dpsi*) from the dS_2/dpsi* and S_2 summed over every slice."""
+    if dS.dtype != torch.complex128 or not dS.is_cuda or not dS.is_contiguous():
+        raise ValueError("dS must be a contiguous complex128 CUDA tensor")
+    N = _check_state(dS)
+    g = torch.empty(dS.numel(), dtype=dtype, device=dS.device)
+    c = _ctx(dS)
+    M = ctypes.c_double()
+    c.check(c.lib.hadamag_sre_grad_combine(c.h, ctypes.c_void_p(dS.data_ptr()), N, float(S2), _dtype_code(g),
+                                           ctypes.byref(M), ctypes.c_void_p(g.data_ptr()), _stream(dS)),
+            "hadamag_sre_grad_combine")
     return M.value, g
 
 

@@ -25,7 +25,8 @@ namespace hm {
 // ------------------------------------------------------------------------------------------
 template <int L>
 __global__ void __launch_bounds__(OnepassShape<L>::NT)
-grad_onepass(const float2* __restrict__ psi, int N, double* __restrict__ sums, float2* __restrict__ gpart) {
+grad_onepass(const float2* __restrict__ psi, int N, double* __restrict__ sums, float2* __restrict__ gpart,
+             int64_t a_base, int64_t count) {
     using Sh = OnepassShape<L>;
     constexpr int G = Sh::G, GPC = Sh::GPC;
     extern __shared__ float2 smem[];
@@ -35,7 +36,7 @@ grad_onepass(const float2* __restrict__ psi, int N, double* __restrict__ sums, f
     const int64_t gg = (int64_t)blockIdx.x * GPC + gi;
     const int64_t dim = int64_t(1) << N;
     double acc = 0.0, acc1 = 0.0;
-    grad_onepass_group<L>(psi, N, gpart + (size_t)gg * dim, gg, ngroups, sm, acc, acc1);
+    grad_onepass_group<L>(psi, N, gpart + (size_t)gg * dim, gg, ngroups, sm, acc, acc1, a_base, count);
     if (t == 0) {
         sums[gg * 3 + 0] = acc;
         sums[gg * 3 + 1] = acc1;
@@ -49,7 +50,8 @@ template <int M>
 __global__ void __launch_bounds__(256, 2) grad_threepass(GradParams P) {
     extern __shared__ float2 smem[];
     const uint32_t tid = threadIdx.x;
-    const G3State S{P.psi, P.N, P.scratch, P.R, P.A, P.U, P.n_batches, P.p1, P.p2, P.p3, P.done1, P.done2, P.done3};
+    const G3State S{P.psi, P.N, P.scratch, P.R, P.A, P.U, P.n_batches, P.p1, P.p2, P.p3, P.done1, P.done2, P.done3,
+                    P.a_base};
     const G3Ctl C{P.status, P.spin_limit, P.wait_bias};
     const int64_t dim = int64_t(1) << P.N;
     const int64_t per_stage = (int64_t)P.p1 + P.p2 + P.p3;
@@ -97,21 +99,48 @@ __global__ void grad_finalize(const float2* __restrict__ gpart, int64_t nparts, 
     }
 }
 
+// dS[z] = sum over partials of dS/dpsi*_z (FP64, in partial order), unscaled: the part of
+// the gradient contributed by one slice of X-strings.
+__global__ void grad_sum_parts(const float2* __restrict__ gpart, int64_t nparts, int64_t dim,
+                               double2* __restrict__ out) {
+    for (int64_t z = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; z < dim; z += (int64_t)gridDim.x * blockDim.x) {
+        double gx = 0.0, gy = 0.0;
+        for (int64_t k = 0; k < nparts; ++k) {
+            const float2 v = gpart[(size_t)k * dim + z];
+            gx += v.x;
+            gy += v.y;
+        }
+        out[z] = make_double2(gx, gy);
+    }
+}
+
+// grad[z] = -dS[z] / (ln 2 * S_2) from the summed dS/dpsi* of every slice.
+template <class TOut>
+__global__ void grad_scale(const double2* __restrict__ dS, int64_t dim, double S2, TOut* __restrict__ out) {
+    const double scale = -1.0 / (0.69314718055994530942 * S2);
+    for (int64_t z = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; z < dim; z += (int64_t)gridDim.x * blockDim.x) {
+        const double2 v = dS[z];
+        if constexpr (sizeof(TOut) == 8) out[z] = make_float2((float)(v.x * scale), (float)(v.y * scale));
+        else out[z] = make_double2(v.x * scale, v.y * scale);
+    }
+}
+
 // ------------------------------------------------------------------------------------------
 template <int L>
 static cudaError_t launch_grad_onepass_t(const float2* psi, int N, double* sums, float2* gpart, int groups_max,
-                                         int* ngroups, cudaStream_t st) {
+                                         int* ngroups, cudaStream_t st, int64_t a_base, int64_t count) {
     using Sh = OnepassShape<L>;
     size_t smem = (size_t)Sh::GPC * (L >= 5 ? tile_slots(L) : (1u << L)) * sizeof(float2);
     auto k = grad_onepass<L>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int grid = groups_max / Sh::GPC;
-    const int64_t need = ((int64_t(1) << (L + 1)) + Sh::GPC - 1) / Sh::GPC;
+    const int64_t cnt = count < 0 ? (int64_t(1) << (L + 1)) : count;
+    const int64_t need = (cnt + Sh::GPC - 1) / Sh::GPC;
     if (grid > need) grid = (int)need;
     if (grid < 1) grid = 1;
     *ngroups = grid * Sh::GPC;
-    k<<<grid, Sh::NT, smem, st>>>(psi, N, sums, gpart);
+    k<<<grid, Sh::NT, smem, st>>>(psi, N, sums, gpart, a_base, count);
     return cudaGetLastError();
 }
 
@@ -126,9 +155,10 @@ int grad_onepass_gpc(int N) {
 }
 
 cudaError_t launch_grad_onepass(const float2* psi, int N, double* sums, float2* gpart, int groups_max,
-                                int* ngroups, cudaStream_t st) {
+                                int* ngroups, cudaStream_t st, int64_t a_base, int64_t count) {
     switch (N - 1) {
-#define HM_CASE(LL) case LL: return launch_grad_onepass_t<LL>(psi, N, sums, gpart, groups_max, ngroups, st);
+#define HM_CASE(LL) \
+    case LL: return launch_grad_onepass_t<LL>(psi, N, sums, gpart, groups_max, ngroups, st, a_base, count);
         HM_CASE(0) HM_CASE(1) HM_CASE(2) HM_CASE(3) HM_CASE(4) HM_CASE(5) HM_CASE(6) HM_CASE(7)
         HM_CASE(8) HM_CASE(9) HM_CASE(10) HM_CASE(11) HM_CASE(12) HM_CASE(13) HM_CASE(14)
 #undef HM_CASE
@@ -180,6 +210,21 @@ cudaError_t launch_grad_finalize(const float2* gpart, int64_t nparts, int64_t di
     if (blocks > 4096) blocks = 4096;
     if (c128) grad_finalize<double2><<<(unsigned)blocks, 256, 0, st>>>(gpart, nparts, dim, s2, (double2*)out);
     else grad_finalize<float2><<<(unsigned)blocks, 256, 0, st>>>(gpart, nparts, dim, s2, (float2*)out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_sum_parts(const float2* gpart, int64_t nparts, int64_t dim, double2* out, cudaStream_t st) {
+    int64_t blocks = (dim + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    grad_sum_parts<<<(unsigned)blocks, 256, 0, st>>>(gpart, nparts, dim, out);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_grad_scale(const double2* dS, int64_t dim, double S2, void* out, bool c128, cudaStream_t st) {
+    int64_t blocks = (dim + 255) / 256;
+    if (blocks > 4096) blocks = 4096;
+    if (c128) grad_scale<double2><<<(unsigned)blocks, 256, 0, st>>>(dS, dim, S2, (double2*)out);
+    else grad_scale<float2><<<(unsigned)blocks, 256, 0, st>>>(dS, dim, S2, (float2*)out);
     return cudaGetLastError();
 }
 

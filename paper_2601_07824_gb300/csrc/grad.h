@@ -3,6 +3,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include "ctx.h"
 #include "sre_fwd.h"
 
 namespace hm {
@@ -22,14 +23,21 @@ struct GradParams {
     unsigned wait_bias;
     float2* gpart;           // per-CTA partial dS_2/dpsi* [grid][2^N] (zeroed before launch)
     double* sums;            // per-CTA [grid][3]: S_2, S_1, 0
+    int64_t a_base = 0;      // X-strings a_base .. a_base + A n_batches - 1
 };
 
 int grad_onepass_gpc(int N);
+// X-strings a_base .. a_base + count - 1 (count < 0: all 2^N)
 cudaError_t launch_grad_onepass(const float2* psi, int N, double* sums, float2* gpart, int groups_max,
-                                int* ngroups, cudaStream_t st);
+                                int* ngroups, cudaStream_t st, int64_t a_base = 0, int64_t count = -1);
 cudaError_t grad_threepass_grid(int N, int sm_count, int* grid);
 cudaError_t launch_grad_threepass(const GradParams& P, int grid, cudaStream_t st);
+cudaError_t launch_grad_sum_parts(const float2* gpart, int64_t nparts, int64_t dim, double2* out, cudaStream_t st);
+cudaError_t launch_grad_scale(const double2* dS, int64_t dim, double S2, void* out, bool c128, cudaStream_t st);
 cudaError_t launch_grad_finalize(const float2* gpart, int64_t nparts, int64_t dim, const double* s2, void* out,
                                  bool c128, cudaStream_t st);
+
+hadamag_status enqueue_grad_parts(hadamag_ctx_t c, const float2* p, int N, int64_t a0, int64_t count, cudaStream_t st,
+                                  int64_t* nparts_out);
 
 }  // namespace hm

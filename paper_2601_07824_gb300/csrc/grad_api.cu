@@ -9,9 +9,11 @@ using namespace hm;
 
 namespace hm {
 
-// Enqueues the adjoint: gradient written to grad_out (same dtype as `dt`), and the FP64 sums
-// [S_2, S_1, 0] left in c->res (device).  No host synchronisation.
-hadamag_status enqueue_grad(hadamag_ctx_t c, const float2* p, int N, void* grad_out, bool c128, cudaStream_t st) {
+// Enqueues the adjoint kernels over the X-strings a0 .. a0 + count - 1: per-part FP32 partial
+// gradients dS_2/dpsi* in c->grad_acc and per-part FP64 sums [S_2, S_1, 0] in c->part
+// (*nparts parts).  For 16 <= N, a0 and count must be multiples of 8.  No host synchronisation.
+hadamag_status enqueue_grad_parts(hadamag_ctx_t c, const float2* p, int N, int64_t a0, int64_t count, cudaStream_t st,
+                                  int64_t* nparts_out) {
     hadamag_status s;
     cudaError_t e;
     const int64_t dim = int64_t(1) << N;
@@ -27,7 +29,7 @@ hadamag_status enqueue_grad(hadamag_ctx_t c, const float2* p, int N, void* grad_
         if ((e = cudaMemsetAsync(c->grad_acc.ptr, 0, (size_t)groups_max * dim * sizeof(float2), st)) != cudaSuccess)
             return cuda_fail(c, e, "memset partials");
         int ng = 0;
-        e = launch_grad_onepass(p, N, (double*)c->part.ptr, (float2*)c->grad_acc.ptr, groups_max, &ng, st);
+        e = launch_grad_onepass(p, N, (double*)c->part.ptr, (float2*)c->grad_acc.ptr, groups_max, &ng, st, a0, count);
         c->launches++;
         if (e != cudaSuccess) return cuda_fail(c, e, "grad_onepass");
         nparts = ng;
@@ -38,7 +40,8 @@ hadamag_status enqueue_grad(hadamag_ctx_t c, const float2* p, int N, void* grad_
         int A = 8;
         while (A > 1 && (size_t)A * per_a > ((size_t)16 << 20)) A >>= 1;
         P.psi = p; P.N = N; P.R = 3; P.A = A; P.U = 8 / A;
-        P.n_batches = dim / A;
+        P.n_batches = count / A;
+        P.a_base = a0;
         P.p1 = (1 << M) / (P.U * 2);
         P.p2 = A * (1024 >> (13 - M));
         P.p3 = A * ((1 << M) / 16);
@@ -62,6 +65,18 @@ hadamag_status enqueue_grad(hadamag_ctx_t c, const float2* p, int N, void* grad_
         if (e != cudaSuccess) return cuda_fail(c, e, "grad_threepass");
         nparts = grid;
     }
+    *nparts_out = nparts;
+    return HADAMAG_OK;
+}
+
+// Enqueues the adjoint: gradient written to grad_out (same dtype as `dt`), and the FP64 sums
+// [S_2, S_1, 0] left in c->res (device).  No host synchronisation.
+hadamag_status enqueue_grad(hadamag_ctx_t c, const float2* p, int N, void* grad_out, bool c128, cudaStream_t st) {
+    hadamag_status s;
+    cudaError_t e;
+    const int64_t dim = int64_t(1) << N;
+    int64_t nparts = 0;
+    if ((s = enqueue_grad_parts(c, p, N, 0, dim, st, &nparts))) return s;
     e = launch_sum_triples((const double*)c->part.ptr, nparts, (double*)c->res.ptr, st);
     c->launches++;
     if (e != cudaSuccess) return cuda_fail(c, e, "sum_triples");

@@ -21,6 +21,7 @@ struct G3State {
     unsigned* done1;
     unsigned* done2;
     unsigned* done3;
+    int64_t a_base = 0;  // X-string of batch 0, entry 0 (a slice [a_base, a_base + A n_batches))
 };
 
 struct G3Ctl {
@@ -65,7 +66,7 @@ __device__ __forceinline__ bool g3_pass1(const G3State& S, const G3Ctl& C, int64
         return false;
     const int a_idx = warp % S.A;
     const int64_t unit = ((int64_t)r * S.U + warp / S.A) * 2;
-    const int64_t a = g * S.A + a_idx;
+    const int64_t a = S.a_base + g * S.A + a_idx;
     const int64_t dim = int64_t(1) << S.N;
     if (a < dim) {
         float2* sbase = S.scratch + (size_t)slot * S.A * ((size_t)1 << L);
@@ -103,7 +104,7 @@ __device__ __forceinline__ bool g3_pass2(const G3State& S, const G3Ctl& C, int64
     if (!cta_wait_geq(S.done1 + slot, (unsigned)((g / S.R + 1) * S.p1) + C.wait_bias, C.status, C.spin_limit))
         return false;
     const int a_idx = r / TILES, tile = r % TILES;
-    const int64_t a = g * S.A + a_idx;
+    const int64_t a = S.a_base + g * S.A + a_idx;
     if (a < (int64_t(1) << S.N)) {
         float2* src = S.scratch + (size_t)slot * S.A * ((size_t)1 << L) + (size_t)a_idx * ((size_t)1 << L) +
                       (size_t)tile * T;
@@ -170,7 +171,7 @@ __device__ __forceinline__ bool g3_pass3(const G3State& S, const G3Ctl& C, int64
     constexpr int PER_A = (1 << M) / 16;
     const int a_idx = r / PER_A;
     const int64_t unit0 = (int64_t)(r % PER_A) * 16 + warp * 2;
-    const int64_t a = g * S.A + a_idx;
+    const int64_t a = S.a_base + g * S.A + a_idx;
     if (a < (int64_t(1) << S.N)) {
         const float2* sbase = S.scratch + (size_t)slot * S.A * ((size_t)1 << L) + (size_t)a_idx * ((size_t)1 << L);
         float2* sm = smem + warp * tile_slots(10);
@@ -210,12 +211,13 @@ __device__ __forceinline__ bool g3_pass3(const G3State& S, const G3Ctl& C, int64
 }
 
 // One-pass adjoint of a whole state by one group of threads (see grad.cu): X-strings
-// a = gg, gg + ngroups, ...; contributions go to gp (this group's partial, 2^N values);
-// the group leader (t == 0) receives the group's S_2 and S_1 sums.  FWD: the sums only.
+// a = a_base + i for i = gg, gg + ngroups, ... below count (count < 0: all 2^N X-strings);
+// contributions go to gp (this group's partial, 2^N values); the group leader (t == 0)
+// receives the group's S_2 and S_1 sums.  FWD: the sums only.
 template <int L, bool FWD = false>
 __device__ __forceinline__ void grad_onepass_group(const float2* __restrict__ psi, int N, float2* __restrict__ gp,
                                                    int64_t gg, int64_t ngroups, float2* sm, double& acc,
-                                                   double& acc1) {
+                                                   double& acc1, int64_t a_base = 0, int64_t count = -1) {
     using Sh = OnepassShape<L>;
     constexpr int E = Sh::E, G = Sh::G;
     using S = TileSched<L, 0, E>;
@@ -223,10 +225,12 @@ __device__ __forceinline__ void grad_onepass_group(const float2* __restrict__ ps
     __shared__ float red[16][2];
     const uint32_t tid = threadIdx.x, t = tid % G;
     const int64_t dim = int64_t(1) << N;
-    const int64_t iters = (dim + ngroups - 1) / ngroups;
+    const int64_t cnt = count < 0 ? dim : count;
+    const int64_t iters = (cnt + ngroups - 1) / ngroups;
     for (int64_t it = 0; it < iters; ++it) {
-        const int64_t a = gg + it * ngroups;
-        const bool valid = a < dim;
+        const int64_t i = gg + it * ngroups;
+        const int64_t a = a_base + i;
+        const bool valid = i < cnt && a < dim;
         const int64_t av = valid ? a : 0;
         const int p = av ? msb64(av) : 0;
         float2 x[1 << E];
