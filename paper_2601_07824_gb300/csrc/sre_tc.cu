@@ -9,8 +9,10 @@
 //     block 2: bits [7, 13) -- rows (bits 0..6) x K = 64, per re/im, times H_64
 //   pass 2 (tile = 128 fibres along bits [13, 20), bits [20, L) butterflied in registers first):
 //     block 3: bits [13, 20) -- rows (fibres) x K = 128, times H_128, then sum |.|^{2n}.
-// Precision form: every operand x is split as x = hi + lo, hi = fp16(x), lo = fp16(x - hi);
-// D = hi*H + lo*H accumulates in fp32 in tensor memory.  The state is first scaled by a power
+// Precision form: every operand x is split as x = hi + 2^-11 lo, hi = fp16(x),
+// lo = fp16(2^11 (x - hi)) (a normal fp16 number wherever x is, so ~22 significant bits);
+// D = hi*H + 2^-11 lo*H accumulates in fp32 in tensor memory (the 2^-11 is the MMA's
+// scale-input-d).  The state is first scaled by a power
 // of two 2^f (chosen from max|psi|^2) so that every fp16 operand stays in range; the per-CTA
 // FP64 sums are unscaled exactly at the end.  FP64 is used only for the cross-tile sums.
 //
@@ -63,15 +65,18 @@ constexpr uint32_t ID_B1 = tc::idesc_f16(128, 128, true, false);
 constexpr uint32_t ID_B2 = tc::idesc_f16(128, 64, true, false);
 constexpr uint32_t ID_B3 = tc::idesc_f16(128, 128, true, false);
 
-// D (+)= [A_hi | A_lo] x [H; H] over NK K-steps of 16 (the hi/lo split as a longer K).
+// D = (A_hi + 2^-LO_SHIFT A_lo) x H over NK K-steps of 16 (the hi/lo split as a longer K): the lo
+// steps accumulate A_lo x H first, then the first hi step scales that partial sum by
+// 2^-LO_SHIFT (scale-input-d, exact in fp32) while adding its own product.
 template <int NK, uint32_t LBO, uint32_t SBO, uint32_t STEP, uint32_t LAYOUT>
 __device__ __forceinline__ void issue_block(uint32_t d, uint32_t a_hi, uint32_t a_lo, uint32_t h, uint32_t idesc) {
 #pragma unroll
     for (int j = 0; j < NK; ++j)
-        tc::mma_f16(d, tc::sdesc(a_hi + j * STEP, LBO, SBO, LAYOUT), tc::sdesc(h + j * KM_STEP, KM_LBO, KM_SBO), idesc, j > 0);
+        tc::mma_f16(d, tc::sdesc(a_lo + j * STEP, LBO, SBO, LAYOUT), tc::sdesc(h + j * KM_STEP, KM_LBO, KM_SBO), idesc, j > 0);
+    tc::mma_f16_scale_d<tc::LO_SHIFT>(d, tc::sdesc(a_hi, LBO, SBO, LAYOUT), tc::sdesc(h, KM_LBO, KM_SBO), idesc);
 #pragma unroll
-    for (int j = 0; j < NK; ++j)
-        tc::mma_f16(d, tc::sdesc(a_lo + j * STEP, LBO, SBO, LAYOUT), tc::sdesc(h + j * KM_STEP, KM_LBO, KM_SBO), idesc, true);
+    for (int j = 1; j < NK; ++j)
+        tc::mma_f16(d, tc::sdesc(a_hi + j * STEP, LBO, SBO, LAYOUT), tc::sdesc(h + j * KM_STEP, KM_LBO, KM_SBO), idesc, true);
 }
 
 // Block-1 operand row group: 8 fibres (m6 = 8 consecutive values, re and im) at K = n, split

@@ -39,6 +39,17 @@ __device__ __forceinline__ void mma_f16(uint32_t d_tmem, uint64_t a, uint64_t b,
         "l"(a), "l"(b), "r"(idesc), "r"((uint32_t)accumulate));
 }
 
+// D[tmem] = A[smem] x B[smem] + D * 2^-SCALE (the instruction's scale-input-d operand, kind::f16
+// and kind::tf32 only, 0 <= SCALE <= 15), one elected thread.
+template <int SCALE>
+__device__ __forceinline__ void mma_f16_scale_d(uint32_t d_tmem, uint64_t a, uint64_t b, uint32_t idesc) {
+    static_assert(SCALE >= 0 && SCALE <= 15, "scale-input-d is 0..15");
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, 1, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p, %4;\n}" ::"r"(d_tmem),
+        "l"(a), "l"(b), "r"(idesc), "n"(SCALE));
+}
+
 // Arrive on `mbar` once every MMA issued so far by this thread has completed.
 __device__ __forceinline__ void commit(uint64_t* mbar) {
     asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(mbar))
@@ -101,14 +112,23 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
-// x = hi + lo with hi = fp16(x) and lo = fp16(x - hi): 8 fp32 values -> two 16-byte rows.
+// Exponent offset of the lo part of the hi/lo split.
+constexpr int LO_SHIFT = 11;
+
+// x = hi + 2^-LO_SHIFT lo with hi = fp16(x) and lo = fp16(2^LO_SHIFT (x - hi)): 8 fp32 values ->
+// two 16-byte rows.  x - hi is exact in fp32 and |x - hi| <= 2^-11 |x|, so lo has the magnitude
+// of x and stays a normal fp16 number down to |x| ~ 2^-14: the pair keeps ~22 significant bits
+// over the whole normal fp16 range of x (a lo part stored unscaled would turn subnormal below
+// |x| ~ 2^-3 and keep only an absolute precision of 2^-25).  The MMAs undo the offset through
+// scale-input-d (issue_block in sre_tc.cu).
 __device__ __forceinline__ void split8(const float* x, uint4& hi, uint4& lo) {
     uint32_t h[4], l[4];
+    const float2 sc = make_float2((float)(1 << LO_SHIFT), (float)(1 << LO_SHIFT));
 #pragma unroll
     for (int k = 0; k < 4; ++k) {
         const __half2 hh = __floats2half2_rn(x[2 * k], x[2 * k + 1]);
         const float2 hf = __half22float2(hh);
-        const float2 r = __fadd2_rn(make_float2(x[2 * k], x[2 * k + 1]), make_float2(-hf.x, -hf.y));
+        const float2 r = __fmul2_rn(__fadd2_rn(make_float2(x[2 * k], x[2 * k + 1]), make_float2(-hf.x, -hf.y)), sc);
         const __half2 ll = __floats2half2_rn(r.x, r.y);
         h[k] = *reinterpret_cast<const uint32_t*>(&hh);
         l[k] = *reinterpret_cast<const uint32_t*>(&ll);

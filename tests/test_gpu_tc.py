@@ -2,8 +2,8 @@
 on tcgen05 tensor cores (fp16 hi/lo operands, fp32 accumulation in tensor memory), 21 <= N <= 24.
 
 Tolerances.  Per-X-string sums: 2e-5 relative of the FP64 oracle, the bound used for the FP32
-CUDA-core path (each operand keeps ~22 significant bits after the hi/lo split, the accumulation
-is fp32).  M_n: |dM| <= 1e-6 * max(1, |M|) against closed forms and against the CUDA-core path,
+CUDA-core path (each operand keeps ~22 significant bits after the hi/lo split, whose lo part
+carries its own 2^11 scale, and the accumulation is fp32).  M_n: |dM| <= 1e-6 * max(1, |M|) against closed forms and against the CUDA-core path,
 which is itself pinned to the oracle."""
 import math
 
@@ -88,14 +88,9 @@ def test_tc_closed_forms_N21(golden):
         assert abs(M) < 1e-6 and abs(ln) < 1e-6
 
 
-def test_tc_product_state_additivity_N21():
-    # M_n is additive over tensor factors: a random product state's M_2 is the sum of its
-    # single-qubit values, each given by the oracle at N = 1.  The amplitudes of a random product
-    # state spread over many decades; values far below the largest one keep only the absolute
-    # precision of the fp16 lo part (2^-25 of the scale), so the tensor path is held to 3e-6
-    # here while the CUDA-core path meets 1e-6 on the same state.
-    N = 21
-    rng = np.random.default_rng(2202)
+def random_product_state(N, seed):
+    """A random product state and the oracle's single-qubit M_2 of each factor."""
+    rng = np.random.default_rng(seed)
     sites = []
     for _ in range(N):
         v = rng.normal(size=2) + 1j * rng.normal(size=2)
@@ -103,13 +98,42 @@ def test_tc_product_state_additivity_N21():
     psi = sites[0]
     for v in sites[1:]:
         psi = np.kron(v, psi)  # qubit j = bit j
-    want = sum(oracle.sre(v, 2.0)[0] for v in sites)
-    t = on_dev(psi.astype(np.complex64))
+    return psi.astype(np.complex64), sum(oracle.sre(v, 2.0)[0] for v in sites)
+
+
+def test_tc_product_state_additivity_N21():
+    # M_n is additive over tensor factors: a random product state's M_2 is the sum of its
+    # single-qubit values, each given by the oracle at N = 1.  The amplitudes of a random product
+    # state spread over many decades, which tests the hi/lo split far below the largest value.
+    N = 21
+    psi, want = random_product_state(N, 2202)
+    t = on_dev(psi)
     M, ln = hm.sre(t, 2.0, path=PATH_TENSOR)
-    assert close_M(M, want, 3e-6), (M, want)
+    assert close_M(M, want), (M, want)
     assert abs(ln) < 1e-6
     Mc, _ = hm.sre(t, 2.0, path=PATH_CUDACORE)
     assert close_M(Mc, want), (Mc, want)
+
+
+@pytest.mark.parametrize("path", [PATH_TENSOR, PATH_CUDACORE], ids=["tensor", "cudacore"])
+@pytest.mark.parametrize("state", ["t_product", "ghz", "random_product"])
+def test_full_size_closed_forms_N22(golden, path, state):
+    # exact M_2 of whole N = 22 states on both paths against values fixed independently of the
+    # GPU: |T>^22 gives 22 log2(4/3) (additivity of the per-qubit closed form), GHZ gives 0
+    # (a stabilizer state), a random product state the sum of the oracle's N = 1 values
+    N = 22
+    if state == "t_product":
+        psi = I.t_state_product(N, dtype=np.complex64)
+        g = golden["closed_forms"]["sre_t_state_per_qubit"]
+        want = N * g["M2"] / g["N"]
+        assert abs(want - N * math.log2(4.0 / 3.0)) < 1e-12
+    elif state == "ghz":
+        psi, want = I.ghz_state(N, dtype=np.complex64), 0.0
+    else:
+        psi, want = random_product_state(N, 2203)
+    M, ln = hm.sre(on_dev(psi), 2.0, path=path)
+    assert close_M(M, want), (state, M, want)
+    assert abs(ln) < 2e-6
 
 
 def test_tc_matches_cudacore_N21():
