@@ -357,21 +357,23 @@ hadamag_status hadamag_sre_batched(hadamag_ctx_t ctx, int count, const void* con
 hadamag_status hadamag_batched_status(hadamag_ctx_t ctx, hadamag_stream_t stream);
 
 /*
- * Allocation-free exact SRE (the paper has no counterpart; this is a calling convenience).
- * For callers that cannot allocate device memory where they need the number: work enqueued
- * during a stream capture in the global capture mode, code whose device memory is entirely
- * owned by a framework pool or fixed budget, and loops that must not pay the device
- * synchronisation of cudaMalloc/cudaFree.  No context is needed and nothing is allocated:
- * the scratch is a fixed 8.06 MiB __device__ array inside the library, held by every GPU
- * that loads the library until the process exits.
+ * Allocation-free exact SRE.  The paper has no counterpart; this is a calling convenience for
+ * callers that cannot allocate device memory where they need the number: code inside a host
+ * application or framework that owns all device memory through its own pool or a budget fixed at
+ * start-up, latency-critical loops that must not pay the device-wide synchronisation of
+ * cudaMalloc / cudaFree, and plugins that must not grow the process's device footprint.  No
+ * context is needed and nothing is allocated: the scratch is a fixed 8.06 MiB __device__ array
+ * inside the library, held by every GPU that loads the library until the process exits.
  *   psi_dev: 2^N complex64 amplitudes on the current device, 16-byte aligned.
- *   16 <= N <= 20 (other N: HADAMAG_ERR_UNSUPPORTED, nothing enqueued); n > 0 as hadamag_sre.
- *   out_dev: 3 doubles on the device, written in stream order: [M_n, lost_norm, status]
- *   (status 0 = ok; otherwise the device-side check bits, and M_n is NaN).
+ *   16 <= N <= 20 (other N: HADAMAG_ERR_UNSUPPORTED, nothing enqueued: the array holds the
+ *   scratch of N = 20 at most); n > 0 as hadamag_sre.
+ *   out_dev: 3 doubles on the device, 8-byte aligned, written in stream order:
+ *   [M_n, lost_norm, status] (status 0 = ok; otherwise the device-side check bits, and M_n is NaN).
  * The call enqueues its kernels on `stream` and returns without synchronising.  Every call
  * on a device shares the same array (it keeps the last call's contents; each call clears
  * what must start at zero), so calls that overlap on the GPU race: serialise them.  The
- * first call on a device looks up the array's address; make it before any stream capture.
+ * first call on a device does the set-up (it looks up the array's address with that device
+ * current); make it before any stream capture.  Not valid on a device after cudaDeviceReset.
  */
 hadamag_status hadamag_sre_noalloc(const void* psi_dev, int N, double n, double* out_dev,
                                    hadamag_stream_t stream);

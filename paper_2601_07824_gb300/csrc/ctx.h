@@ -32,7 +32,7 @@ struct hadamag_ctx_s {
     hm::DevBuf grad_acc, batch_meta, batch_sums, tc_scratch, ti_state, rdm_idx;
     double* host_res = nullptr;
     int* host_status = nullptr;
-    long long spin_limit = 1ll << 25;
+    long long spin_limit = hm::kDefaultSpinLimit;
     unsigned wait_bias = 0;
     int autotune = 1;
     int fp32_powers = 0;  // non-integer n: FP32 powers (mode 4) where n <= 4 and n (N + 2) <= 100

@@ -1,22 +1,27 @@
 // noalloc.cu -- an allocation-free variant of the exact-SRE call (two-pass kernel, 16 <= N <= 20).
+// The paper has no counterpart; this is a calling convenience.
 //
 // Some callers cannot allocate device memory at the point where they want this number:
-// code that enqueues work while a stream is being captured in the global capture mode
-// (where cudaMalloc is an error), code whose device memory is entirely owned by a framework
-// pool or a fixed budget set at start-up, and latency-critical loops that must not pay the
-// implicit device synchronisation of cudaMalloc/cudaFree.  hadamag_sre_noalloc serves them:
-// it needs no context and no caller scratch, and it calls no allocating routine.  Its
-// scratch (the pass-1/pass-2 ring, the dependency counters, the status word and the per-CTA
-// partial sums) lives in one file-scope __device__ array of fixed size, which every GPU that
-// loads this library keeps until the process exits.
+//   * code running inside a host application or framework that owns all of the device's memory
+//     through its own pool or a budget fixed at start-up, where an extra cudaMalloc either fails
+//     or is not permitted;
+//   * latency-critical loops that must not pay the implicit device-wide synchronisation of
+//     cudaMalloc / cudaFree;
+//   * plugins that must not change the process's device-memory footprint after they load.
+// hadamag_sre_noalloc serves them: it needs no context and no caller scratch, and it calls no
+// allocating routine.  Its scratch (the pass-1/pass-2 ring, the dependency counters, the status
+// word and the per-CTA partial sums) lives in one file-scope __device__ array of fixed size
+// (kBytes, 8.06 MiB), which every GPU that loads this library keeps until the process exits.
 //
 // Consequences a caller has to respect:
 //   * The array is shared by every call on a device and keeps the last call's contents; each
 //     call clears the counters and the status word it relies on.  Calls whose execution
 //     overlaps on the GPU (different streams, or different host threads) race on the array:
 //     serialise them.
-//   * The first call on a device looks up the array's device address (cudaGetSymbolAddress,
-//     with that device current); make that first call before any stream capture.
+//   * The first call on a device does the set-up: with that device current it looks up the
+//     array's device address (cudaGetSymbolAddress) and caches it for the life of the process.
+//     Make that first call before any stream capture.  The cached address does not survive
+//     cudaDeviceReset: do not use this call on a device after resetting it.
 #include <cmath>
 #include <mutex>
 
@@ -103,7 +108,7 @@ extern "C" hadamag_status hadamag_sre_noalloc(const void* psi_dev, int N, double
     P.done1 = reinterpret_cast<unsigned*>(base + kCounterOff);
     P.done2 = P.done1 + 64;
     P.status = reinterpret_cast<int*>(base + kStatusOff);
-    P.spin_limit = 1ll << 25;
+    P.spin_limit = kDefaultSpinLimit;
     P.wait_bias = 0;
     P.out = reinterpret_cast<double*>(base + kPartOff);
     P.per_a = 0;

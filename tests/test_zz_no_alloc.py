@@ -1,8 +1,10 @@
-"""hadamag_sre_noalloc -- the allocation-free exact-SRE call for callers that cannot
-allocate device memory (stream capture in global mode, framework-owned memory pools,
-allocation-free loops) -- checked through the C ABI against hadamag_sre on two calls in a
-row.  This file is collected last on purpose: the call keeps its scratch in a library-wide
-device array, and the checks must hold both in a fresh process and after every other test."""
+"""hadamag_sre_noalloc -- the allocation-free exact-SRE call, for callers that cannot allocate
+device memory where they need M_n (a host framework that owns all device memory through its own
+pool or a fixed budget, latency-critical loops that must not pay cudaMalloc's device-wide
+synchronisation, plugins that must not grow the device footprint) -- checked through the C ABI
+against hadamag_sre on two calls in a row.  This file is collected last on purpose: the call
+keeps its scratch in a library-wide device array, and the checks must hold both in a fresh
+process and after every other test."""
 import ctypes
 
 import numpy as np
