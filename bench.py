@@ -6,11 +6,17 @@ Default workload (one step = one complete exact M_2 of one state, every X-string
   FP32 CUDA-core Walsh-Hadamard path, 4^20 = 1.1e12 Pauli strings per step.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
-                  [--N 20] [--path cudacore|tensor] [--no-cpu-baseline] [--extra] [--xstrings K]
+                  [--N 20] [--path cudacore|tensor] [--no-cpu-baseline] [--no-lines] [--extra] [--xstrings K]
 
-Multi-GPU (torchrun, one rank per GPU): the X-strings are independent (Sec. 3.1.2), so every
-rank runs the same per-state work on its own replica ("scaling": "weak", no collective on
-the data path); rank 0 prints the JSON line with the max time over ranks.
+The same line carries the metric's other configurations ("lines"): exact M2 at N = 22 on the
+CUDA-core and the tensor-core paths and exact mana at N = 11, each with its clocks, roofline
+fraction and error against an independent value.
+
+Multi-GPU (torchrun, one rank per GPU): the X-strings are independent (Sec. 3.1.2; Sec. 4.1
+splits them over ranks and GPUs), so the ranks split the one state's X-strings into
+chunk-aligned slices, all-gather the per-chunk FP64 sums over NCCL and combine them in chunk
+order ("scaling": "strong": the work per step is fixed); rank 0 prints the JSON line with the
+max time over ranks.
 """
 from __future__ import annotations
 
@@ -45,6 +51,8 @@ def parse():
                          "mixed-state mana N=8, even-sector SRE N=20, qudit mana d=5, mana gradient")
     ap.add_argument("--only", default="",
                     help="run just the named --extra workloads (comma-separated, e.g. ti_N20_L10) and print them")
+    ap.add_argument("--no-lines", action="store_true",
+                    help="skip the metric's other configurations (N = 22 on both paths, mana N = 11)")
     ap.add_argument("--no-new-rows", action="store_true",
                     help="skip the separate-process timing of the Algorithm 3 / 6, sector and qudit workloads")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
@@ -65,14 +73,22 @@ def workload_state(N: int):
 
 
 # DRAM bytes (read + write) of one launch of the dominant kernel, from one ncu capture of this
-# exact command (profiles/sre_twopass_N20_bench_dram.md); absent for other workloads.
-TRAFFIC = {(20, 0): 188614912 + 26648091904}
+# exact command on the current kernel (profiles/); absent (null) when no capture matches it.
+TRAFFIC = {}
 
 
 def ops_per_string(N: int) -> int:
-    # FP32 operations per Pauli string (FMA counted once) in the half-length form:
-    # (N-1) butterfly stages, 2 for the pair product, 3 for the |c|^4 and |c|^2 reduction.
-    return N + 4
+    # Algorithmic FP32 operations per Pauli string (FMA counted once) of the method's real
+    # transform (u = Re v + Im v of length 2^N): N butterfly stages, the pair product and u,
+    # and the |c|^4 / |c|^2 reduction -- N + 7.  (The kernels' half-length complex form issues
+    # N + 4: N - 1 stages, 2 for the pair product, 3 for the reduction.)
+    return N + 7
+
+
+def mana_ops_per_point(N: int) -> float:
+    # radix-3 transform: ~14 FP32 operations per 3 complex values per digit (4.7 per value and
+    # digit), plus ~8 for the pair product and |chi| -- about 60 at N = 11
+    return 4.7 * N + 8.0
 
 
 def fp32_peak_ops(sm_count: int, mhz: float) -> float:
@@ -80,10 +96,27 @@ def fp32_peak_ops(sm_count: int, mhz: float) -> float:
 
 
 def tensor_flops_per_string(N: int) -> int:
-    # tensor-core path: each Pauli string is one real value of the half-length transform; its
-    # Kronecker blocks are K = 128, 64 and 128 wide (pass 1: 7 + 6 bits, pass 2: 7 bits), each
-    # applied to the hi and the lo operand: 2 (hi, lo) x 2 (multiply-add) x (128 + 64 + 128)
+    # tensor-core path as issued: each Pauli string is one real value of the half-length
+    # transform; its Kronecker blocks are K = 128, 64 and 128 wide (pass 1: 7 + 6 bits, pass 2:
+    # 7 bits), each applied to the hi and the lo operand: 2 (hi, lo) x 2 (multiply-add) x
+    # (128 + 64 + 128)
     return 4 * (128 + 64 + 128)
+
+
+def tensor_alg_flops_per_string(N: int) -> int:
+    # algorithmic tensor work of the method: H_16 blocks (4 bits each) on hi/lo operands,
+    # 2 x 2 x 16 = 64 FLOPs per value per 4 stages -> 16 N per Pauli string
+    return 16 * N
+
+
+def golden_value(key: str):
+    """A stored FP64 oracle value for a full-size workload (tests/golden/oracle_full_size.json,
+    written by tests/golden/make_full_size_values.py), or None."""
+    try:
+        with open(os.path.join(ROOT, "tests", "golden", "oracle_full_size.json")) as f:
+            return json.load(f).get(key)
+    except (OSError, ValueError):
+        return None
 
 
 def measured_peak(key: str, fallback: float):
@@ -292,6 +325,11 @@ def main():
     if args.xstrings > 0:
         alist = torch.arange(args.xstrings, dtype=torch.int64, device=dev)
         step = lambda: (hm.sre_terms(psi, 2.0, alist), None)  # noqa: E731
+    elif world > 1:
+        # one state split by X-string over the ranks (strong scaling): each rank evaluates its
+        # slice, the ranks all-gather the per-chunk FP64 triples (NCCL) and combine them in order
+        from paper_2601_07824_gb300 import shard
+        step = lambda: shard.sre_sharded(psi, 2.0, path=path)  # noqa: E731
     else:
         step = lambda: hm.sre(psi, 2.0)  # noqa: E731
     for _ in range(args.warmup):
@@ -314,21 +352,36 @@ def main():
     strings_per_step = 4.0 ** N if args.xstrings <= 0 else float(args.xstrings) * 2 ** N
     if args.xstrings > 0:
         M = ln = None
-    value = aggregate_rate(world, args.steps, strings_per_step, t_max)
+    sharded = world > 1 and args.xstrings <= 0
+    # sharded: the ranks share one state's 4^N strings per step; otherwise every rank does its own
+    value = (args.steps * strings_per_step / t_max) if sharded else aggregate_rate(world, args.steps, strings_per_step,
+                                                                                   t_max)
     clocks = clk.summary()
 
     # end-to-end: the C-ABI host-buffer call, H2D copy from pinned memory inside the timed region
     e2e = None
     if not args.no_e2e and args.xstrings <= 0:
         host = torch.from_numpy(psi_np).pin_memory()
-        hm.sre_host(host.numpy(), 2.0, device=local)
+        if sharded:
+            # every rank copies the state from pinned host memory, evaluates its slice, and the
+            # combined result comes back to the host (sre_combine runs on host doubles)
+            dst = torch.empty_like(psi)
+
+            def e2e_step():
+                dst.copy_(host, non_blocking=True)
+                return shard.sre_sharded(dst, 2.0, path=path)
+        else:
+            def e2e_step():
+                return hm.sre_host(host.numpy(), 2.0, device=local)
+        e2e_step()
         barrier()
         t0 = time.perf_counter()
         for _ in range(args.steps):
-            hm.sre_host(host.numpy(), 2.0, device=local)
+            e2e_step()
         barrier()
         te = max_over_ranks(time.perf_counter() - t0, world, dev)
-        e2e = {"value": aggregate_rate(world, args.steps, strings_per_step, te), "unit": UNIT,
+        e2e = {"value": (args.steps * strings_per_step / te) if sharded
+               else aggregate_rate(world, args.steps, strings_per_step, te), "unit": UNIT,
                "h2d_bytes_per_step": int(psi_np.nbytes), "d2h_bytes_per_step": 3 * 8 + 4}
 
     line = None
@@ -350,16 +403,18 @@ def main():
             peak = fp32_peak_ops(sm_count, mhz_max)
             roof = {"bound": "alu", "achieved": achieved / 1e12, "peak": peak / 1e12, "unit": "TFLOP/s",
                     "frac": achieved / peak, "traffic": TRAFFIC.get((N, args.xstrings)),
-                    "note": f"FP32 ops (FMA = 1) = {ops_per_string(N)} per Pauli string; peak = "
-                            f"{sm_count} SMs x 128 lanes x {mhz_max:.0f} MHz; kernel time = CUDA events "
-                            "around the call on its stream"}
+                    "note": f"algorithmic FP32 ops (FMA = 1) = N + 7 = {ops_per_string(N)} per Pauli string "
+                            f"(the kernel issues N + 4); peak = {sm_count} SMs x 128 lanes x {mhz_max:.0f} MHz; "
+                            "kernel time = CUDA events around the call on its stream"}
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * t_max / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "scaling": "strong" if sharded else "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": (f"exact M2, N={N}: {desc}; complex64; {args.path} Walsh-Hadamard path"
                                     + (f"; first {args.xstrings} X-strings only (profiling)" if args.xstrings > 0 else "")),
                        "N": N, "n": 2, "strings_per_step": strings_per_step,
+                       "parallelism": (f"X-strings split over {world} ranks (chunk-aligned slices, NCCL all-gather "
+                                       "of per-chunk FP64 sums)") if sharded else "one state per GPU",
                        "l2": f"state ({psi_np.nbytes >> 20} MiB) is smaller than L2: a 256 MiB buffer is written between steps",
                        "M2": M, "lost_norm": ln},
             "roofline": roof,
@@ -369,11 +424,19 @@ def main():
         }
         if clocks.get("sm_mhz") and roof["bound"] == "alu":
             line["roofline"]["frac_at_measured_clock"] = achieved / fp32_peak_ops(sm_count, clocks["sm_mhz"])
+        ref = golden_value("sre_brickwork_N20_depth10_seed2001") if (N == 20 and args.xstrings <= 0) else None
+        if ref and M is not None:
+            line["error"] = {"vs": "FP64 oracle on the same complex64 amplitudes (tests/golden/oracle_full_size.json)",
+                             "M2_oracle": ref["M2"], "abs_dM2": abs(M - ref["M2"]),
+                             "rel_dM2": abs(M - ref["M2"]) / max(1.0, abs(ref["M2"])),
+                             "abs_dlost_norm": abs(ln - ref["lost_norm"])}
     if world > 1:
         dist.barrier()
     if rank == 0 and not args.no_cpu_baseline:
         cb, _ = cpu_baseline(psi_np, N, args.cpu_seconds)
         line["cpu_baseline"] = cb
+    if rank == 0 and world == 1 and not args.no_lines and args.xstrings <= 0:
+        line["lines"] = metric_lines(hm, dev, sm_count, flush)
     if rank == 0 and args.extra:
         line["extra"] = extra_workloads(hm, dev, sm_count)
     if rank == 0 and world == 1 and not args.no_new_rows:
@@ -382,6 +445,110 @@ def main():
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+def metric_lines(hm, dev, sm_count, flush, reps: int = 3, frac_log2: int = 3):
+    """The metric's other configurations, after the headline, each with a warm-up, `reps` timed
+    repeats (CUDA events; L2 flushed between repeats), clocks sampled during its repeats, a
+    roofline fraction and an error against an independent value:
+      * exact M2 at N = 22 (i.i.d. Gaussian state, seed 2201) on the FP32 CUDA-core path and
+        on the tensor-core path, each timed on the X-strings [0, 2^22 / 2^frac_log2) through
+        hadamag_sre_slice (the same kernels; a full sum takes 2^frac_log2 times as long);
+        error: the same slice of |T>^22, whose per-X-string sums are 2^-|a| (closed form);
+      * exact mana of N = 11 qutrits (Gaussian, seed 1101), whole sum; error against the
+        stored FP64 oracle value, and the Strange-state closed form N log2(5/3)."""
+    import math
+
+    import numpy as np
+    import torch
+    from paper_2601_07824_gb300 import _lib, inputs
+    out = {}
+    stream = torch.cuda.current_stream(dev)
+
+    def timed(fn):
+        fn()  # warm-up (buffers sized, autotune)
+        torch.cuda.synchronize(dev)
+        ts, r = [], None
+        with ClockSampler(dev.index or 0) as clk:
+            for k in range(reps):
+                flush.fill_(k & 0xFF)
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                r = fn()
+                e1.record(stream)
+                torch.cuda.synchronize(dev)
+                ts.append(e0.elapsed_time(e1) / 1e3)
+        return ts, r, clk.summary()
+
+    N = 22
+    a1 = 2 ** (N - frac_log2)
+    strings = float(a1) * 2 ** N
+    psi = torch.from_numpy(inputs.gaussian_state(N, 2201, dtype=np.complex64)).to(dev)
+    tst = torch.from_numpy(inputs.t_state_product(N, dtype=np.complex64)).to(dev)
+    want_S2, want_S1 = 1.5 ** (N - frac_log2), float(a1)  # sum over a < a1 of 2^-|a|, and of 1
+    tpeak, tsrc = measured_peak("bf16_tflops", 1900.0)
+    res = {}
+    for name, path in (("cudacore", _lib.PATH_CUDACORE), ("tensor", _lib.PATH_TENSOR)):
+        try:
+            ts, ch, clocks = timed(lambda p=path: hm.sre_slice(psi, 2.0, 0, a1, path=p))
+            t = statistics.median(ts)
+            rate = strings / t
+            tch = hm.sre_slice(tst, 2.0, 0, a1, path=path).cpu().numpy()
+            S2, S1 = float(np.sum(tch[:, 0])), float(np.sum(tch[:, 1]))
+            d = {"value": rate, "unit": UNIT, "s_per_call": t, "s_all": ts, "clocks": clocks,
+                 "workload": f"exact M2 sums, N = 22 Gaussian (seed 2201), X-strings [0, 2^{N - frac_log2}) of "
+                             f"2^{N} ({strings:.3e} Pauli strings per call), {name} path",
+                 "S2_slice": float(np.sum(ch[:, 0].cpu().numpy())),
+                 "error": {"vs": "closed form on |T>^22 over the same slice: S2 = 1.5^19, S1 = 2^19",
+                           "rel_dS2": abs(S2 / want_S2 - 1.0), "rel_dS1": abs(S1 / want_S1 - 1.0),
+                           "equiv_abs_dM2": abs(S2 / want_S2 - 1.0) / math.log(2.0)}}
+            if name == "tensor":
+                d["roofline"] = {"bound": "tensor", "unit": "TFLOP/s", "peak": tpeak, "peak_source": f"{tsrc} bf16 burst",
+                                 "achieved": tensor_alg_flops_per_string(N) * rate / 1e12,
+                                 "frac": tensor_alg_flops_per_string(N) * rate / (tpeak * 1e12),
+                                 "count": f"{tensor_alg_flops_per_string(N)} FLOPs per Pauli string (16 N, H_16 "
+                                          "blocks on hi/lo operands)",
+                                 "frac_issued_blocks": tensor_flops_per_string(N) * rate / (tpeak * 1e12),
+                                 "issued": f"{tensor_flops_per_string(N)} FLOPs per Pauli string (blocks K = 128, 64, "
+                                           "128 on hi and lo)"}
+            else:
+                pk = fp32_peak_ops(sm_count, 2070.0)
+                d["roofline"] = {"bound": "alu", "unit": "TFLOP/s", "peak": pk / 1e12,
+                                 "achieved": ops_per_string(N) * rate / 1e12, "frac": ops_per_string(N) * rate / pk,
+                                 "count": f"N + 7 = {ops_per_string(N)} FP32 ops per Pauli string"}
+            res[name] = d
+            out[f"sre_N22_{name}"] = d
+        except Exception as e:  # noqa: BLE001
+            out[f"sre_N22_{name}"] = {"error": str(e)}
+    if "cudacore" in res and "tensor" in res:
+        out["sre_N22_tensor_over_cudacore"] = res["tensor"]["value"] / res["cudacore"]["value"]
+        out["sre_N22_rel_dS2_tensor_vs_cudacore"] = abs(res["tensor"]["S2_slice"] / res["cudacore"]["S2_slice"] - 1.0)
+    del psi, tst
+
+    try:
+        Nq = 11
+        q = torch.from_numpy(inputs.gaussian_state(Nq, 1101, d=3, dtype=np.complex64)).to(dev)
+        ts, r, clocks = timed(lambda: hm.mana(q))
+        t = statistics.median(ts)
+        pts = 9.0 ** Nq
+        pk = fp32_peak_ops(sm_count, 2070.0)
+        d = {"value": pts / t, "unit": "phase-space points/s", "s_per_call": t, "s_all": ts, "clocks": clocks,
+             "workload": "exact mana, N = 11 qutrits, Gaussian (seed 1101), complex64, all 9^11 points",
+             "mana": r[0],
+             "roofline": {"bound": "alu", "unit": "TFLOP/s", "peak": pk / 1e12,
+                          "achieved": mana_ops_per_point(Nq) * pts / t / 1e12,
+                          "frac": mana_ops_per_point(Nq) * pts / t / pk,
+                          "count": f"4.7 N + 8 = {mana_ops_per_point(Nq):.1f} FP32 ops per point"}}
+        ref = golden_value("mana_gaussian_N11_seed1101")
+        strange = hm.mana(torch.from_numpy(inputs.strange_product(Nq, dtype=np.complex64)).to(dev))[0]
+        d["error"] = {"strange_closed_form_abs_dmana": abs(strange - Nq * math.log2(5.0 / 3.0))}
+        if ref:
+            d["error"].update({"vs": "FP64 oracle (tests/golden/oracle_full_size.json)", "mana_oracle": ref["mana"],
+                               "abs_dmana": abs(r[0] - ref["mana"])})
+        out["mana_N11"] = d
+    except Exception as e:  # noqa: BLE001
+        out["mana_N11"] = {"error": str(e)}
+    return out
 
 
 NEW_ROWS = ("ti_N20_L10", "mana_mixed_N8_of_10", "sre_even_sector_N20_u1", "mana_qudit_d5_N6", "mana_grad_d3_N9")

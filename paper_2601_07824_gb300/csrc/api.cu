@@ -92,15 +92,17 @@ TwoPlan plan_twopass(int N) {
     const size_t per_a = ((size_t)1 << L) * sizeof(float2);
     int A = 1;
     if (K1 == 10) {
-        A = 8;  // X-strings per batch: pass-1 warps sharing a pair of state rows
-        while (A > 1 && (size_t)A * per_a > ((size_t)16 << 20)) A >>= 1;
-        p.U = 8 / A;
+        A = 8;  // X-strings per batch: the 8 pass-1 warps share the state rows of two units
+        p.U = 1;
+        // ring slots: 4 while they total <= 64 MiB, else 3 (N = 20: 3 x 32 MiB, inside L2)
+        p.R = ((size_t)4 * A * per_a <= ((size_t)64 << 20)) ? 4 : 3;
     } else {
         p.U = 1;
+        p.R = (N <= 22) ? 4 : 2;
     }
     p.A = A;
-    p.R = (N <= 22) ? 4 : 2;
     p.tiles = twopass_tiles_per_a(N);
+    p.triples = twopass_triples_per_a(N);
     // a pass-1 task covers A X-strings x (U or 1) units per warp x 2 units (K1 = 10);
     // a pass-2 task covers two adjacent column tiles
     p.p1 = (K1 == 10) ? (1 << M) / (p.U * 2) : (1 << M);
@@ -154,7 +156,7 @@ hadamag_status run_sre(hadamag_ctx_t c, const float2* psi, int N, double n, int6
     if (grid > total_tasks) grid = (int)total_tasks;
     if (grid < 1) grid = 1;
     if (per_a) {
-        if ((s = ensure_buf(c, c->tiles, (size_t)count * pl.tiles * 3 * sizeof(double)))) return s;
+        if ((s = ensure_buf(c, c->tiles, (size_t)count * pl.triples * 3 * sizeof(double)))) return s;
         P.out = (double*)c->tiles.ptr;
     } else {
         if ((s = ensure_buf(c, c->part, (size_t)grid * 3 * sizeof(double)))) return s;
@@ -166,7 +168,7 @@ hadamag_status run_sre(hadamag_ctx_t c, const float2* psi, int N, double n, int6
     c->launches++;
     if (e != cudaSuccess) return cuda_fail(c, e, "sre_twopass");
     if (per_a) {
-        e = launch_sum_tiles((double*)c->tiles.ptr, count, pl.tiles, terms, st);
+        e = launch_sum_tiles((double*)c->tiles.ptr, count, pl.triples, terms, st);
         c->launches++;
         if (e != cudaSuccess) return cuda_fail(c, e, "sum_tiles");
     }

@@ -17,7 +17,7 @@ struct DevBuf {
 };
 
 struct TwoPlan {
-    int A, U, R, p1, p2, tiles;
+    int A, U, R, p1, p2, tiles, triples;  // triples: per-X-string output triples (per_a)
     size_t scratch_bytes;
 };
 

@@ -37,6 +37,19 @@ struct PairRows {
             p = a ? msb64(a) : 0;
         }
     }
+    // the same from the two rows staged in shared memory (sA = row A, sB = row B, 2^K1 values each)
+    __device__ __forceinline__ float2 value_rows(const float2* sA, const float2* sB, int64_t a, uint32_t j) const {
+        if (a >> K1) return conj_mul(sB[j ^ (uint32_t)al], sA[j]);
+        const float2* row = (j >> (K1 - 1)) ? sB : sA;
+        const uint32_t lp = j & ((1u << (K1 - 1)) - 1u);
+        if (a != 0) {
+            const uint32_t z = (uint32_t)insert0(lp, p);
+            return conj_mul(row[z ^ (uint32_t)a], row[z]);
+        }
+        const float2 u = row[lp << 1], v = row[(lp << 1) + 1];
+        float e = fmaf(u.x, u.x, u.y * u.y), o = fmaf(v.x, v.x, v.y * v.y);
+        return make_float2(0.5f * (e + o), 0.5f * (e - o));
+    }
     __device__ __forceinline__ float2 value(const float2* __restrict__ psi, int64_t a, uint32_t j) const {
         if (a >> K1) return conj_mul(ld_amp(psi, rowB + (int64_t)(j ^ (uint32_t)al)), ld_amp(psi, rowA + j));
         const int64_t row = (j >> (K1 - 1)) ? rowB : rowA;

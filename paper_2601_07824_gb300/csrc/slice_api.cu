@@ -68,7 +68,7 @@ int64_t chunk_of(int N) { return int64_t(1) << (N < kChunkLog2 ? N : kChunkLog2)
 int64_t batch_of(hadamag_ctx_t c, int N, double n) {
     int64_t per_a = 1;
     if (use_tensor_path(c, N, n)) per_a = tc_triples_per_a(N);
-    else if (N > 15) per_a = twopass_tiles_per_a(N);
+    else if (N > 15) per_a = twopass_triples_per_a(N);
     int64_t b = chunk_of(N);
     while ((size_t)(2 * b) * per_a * 3 * sizeof(double) <= kTileBudget && 2 * b <= (int64_t(1) << N)) b *= 2;
     return b;

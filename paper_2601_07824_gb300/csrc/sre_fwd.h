@@ -69,6 +69,8 @@ cudaError_t launch_hbm(const HbmParams& P, int sm_count, int* grid, cudaStream_t
 // Two-pass geometry for N in [16, 24]: pass 1 transforms K1 = twopass_k1(N) bits (10 or 13),
 // pass 2 the other N-1-K1 bits, in tiles of 2^13 values; tiles per X-string:
 int twopass_tiles_per_a(int N);
+// per-X-string output triples of the two-pass kernel (one per tile and warp)
+inline int twopass_triples_per_a(int N) { return 8 * twopass_tiles_per_a(N); }
 int twopass_k1(int N);
 
 cudaError_t launch_onepass(OnepassArgs& A, int mode, int sm_count, cudaStream_t st);

@@ -17,6 +17,11 @@
 //     finished pass-1 tasks; pass-1 tasks reusing a slot wait for that slot's pass-2 tasks.
 //     Tasks are taken round-robin in a fixed global order in which every task only waits on
 //     earlier tasks, so a co-resident grid cannot deadlock, and the FP64 sums are deterministic.
+//     When the 8 warps of a pass-1 task work on the same two units for 8 X-strings that share
+//     their state rows (8 consecutive X-strings of an aligned batch always do), the 4 rows are
+//     copied once into shared memory (cp.async) and every warp forms its pair products there
+//     instead of issuing its own loads of the same rows.  Pass-2 reductions are per warp (FP32
+//     over the warp's values, FP64 across its tiles), with no CTA barrier per tile.
 #pragma once
 #include "common.cuh"
 #include "pairs.cuh"
@@ -108,25 +113,29 @@ sre_onepass(const float2* __restrict__ psi, int N, double nq, int64_t count,
     }
 }
 
+// Shared-memory slots of the pass-1 row staging (2 units x own/partner row of 2^10 values).
+constexpr uint32_t kStageSlots = 4u << 10;
+
 // ------------------------------------------------------------------------------------------
 // Persistent two-pass kernel, 256 threads per CTA (two CTAs per SM).
 //   K1 = 10: pass 1 is warp-level (each warp one (X-string, unit) of 2^10 values);
 //   K1 = 13: pass 1 is CTA-level (the CTA does one (X-string, unit) of 2^13 values).
 //   The scratch of one X-string is [2^M units][2^K1 columns]; a pass-2 tile is all 2^M units
-//   x 2^(13-M) consecutive columns (2^13 values).
+//   x 2^(13-M) consecutive columns (2^13 values).  Per-X-string output (per_a): one triple per
+//   (tile, warp), [count][TILES][8][3].
+
 template <int K1, int M, int MODE>
 __global__ void __launch_bounds__(256, 2) sre_twopass(TwoPassParams P) {
     using Sh = TwoPassShape<K1, M>;
     constexpr int L = Sh::L, LOGT = Sh::LOGT, T = Sh::T, TILES = Sh::TILES;
     extern __shared__ float2 smem[];
-    __shared__ float red[8][4];
-    __shared__ double redd[8];
+    __shared__ double red64[8][3];
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const float2* __restrict__ psi = P.psi;
     const int64_t dim = int64_t(1) << P.N;
     const int64_t per_stage = (int64_t)P.p1 + P.p2;
     const int64_t total = P.n_batches * per_stage;
-    double acc[3] = {0.0, 0.0, 0.0};
+    double accw[3] = {0.0, 0.0, 0.0};  // lane 0 of each warp: FP64 sums of the warp's tiles
 
     // (stage, kind, index) of a task: stage s runs pass 1 of batch s, then pass 2 of batch s-1.
     auto decode = [&](int64_t task, int64_t& g, int& kind, int& r) {
@@ -193,6 +202,37 @@ __global__ void __launch_bounds__(256, 2) sre_twopass(TwoPassParams P) {
                 if (valid && (tid & (K1 == 10 ? 31 : 255)) == 0) atomicOr(P.status, ST_BADARG);
                 valid = false;
             }
+            bool stage = false;  // CTA-uniform
+            if constexpr (K1 == 10) {
+                if (P.U == 1) {
+                    // every warp on units (unit, unit + 1): rows shared when all X-strings of the
+                    // batch agree in their bits above K1 (always so without a list)
+                    const int64_t i0 = g * P.A;  // < count for every batch
+                    const int64_t a0 = P.a_list ? P.a_list[i0] : i0;
+                    stage = a0 >= 0 && a0 < dim;
+                    if (P.a_list) stage = __syncthreads_and(stage && (!valid || (a >> K1) == (a0 >> K1))) != 0;
+                    if (stage) {
+                        float2* rows = smem + 8 * tile_slots(10);
+                        int64_t rb[4];
+#pragma unroll
+                        for (int uu = 0; uu < 2; ++uu) {
+                            const PairRows<K1, M> pr0(a0, unit + uu);
+                            rb[2 * uu] = pr0.rowA;
+                            rb[2 * uu + 1] = pr0.rowB;
+                        }
+                        // 4 rows x 2^10 values = 2048 16-byte chunks, 8 per thread: chunk
+                        // tid + 256 q is in row q / 2 at value offset 2 (tid + 256 (q % 2))
+#pragma unroll
+                        for (int q = 0; q < 8; ++q) {
+                            const uint32_t off = (tid + 256u * (q & 1)) * 2u;
+                            cp_async16(rows + (q >> 1) * 1024u + off, psi + rb[q >> 1] + off);
+                        }
+                        cp_async_commit();
+                        cp_async_wait<0>();
+                        __syncthreads();
+                    }
+                }
+            }
             if (valid) {
                 float2 x[32];
                 if constexpr (K1 == 10) {
@@ -200,8 +240,14 @@ __global__ void __launch_bounds__(256, 2) sre_twopass(TwoPassParams P) {
                     for (int uu = 0; uu < 2; ++uu) {  // two consecutive units per warp
                         const PairRows<K1, M> pr(a, unit + uu);
                         float2* dst = sbase + (size_t)a_idx * ((size_t)1 << L) + ((size_t)(unit + uu) << K1);
+                        if (stage) {
+                            const float2* rows = smem + 8 * tile_slots(10) + uu * 2048;
 #pragma unroll
-                        for (int k = 0; k < 32; ++k) x[k] = pr.value(psi, a, lane | (k << 5));
+                            for (int k = 0; k < 32; ++k) x[k] = pr.value_rows(rows, rows + 1024, a, lane | (k << 5));
+                        } else {
+#pragma unroll
+                            for (int k = 0; k < 32; ++k) x[k] = pr.value(psi, a, lane | (k << 5));
+                        }
                         reg_fwht<5, 0, 5>(x);
                         tile_rounds<10, 0, 5, 1>(x, sm, lane, SyncWarp());
                         // registers hold j bits [0,5), lanes bits [5,10): store column (k<<5)|lane
@@ -254,31 +300,32 @@ __global__ void __launch_bounds__(256, 2) sre_twopass(TwoPassParams P) {
                 float q = ac.q, s1 = ac.s1, u = ac.u;
                 double qd = ac.qd;
                 warp_sum3<MODE>(q, s1, u, qd, 32);
-                if (lane == 0) { red[warp][0] = q; red[warp][1] = s1; red[warp][2] = u; redd[warp] = qd; }
-                __syncthreads();
-                if (tid == 0) {
-                    double v[3], tot[3] = {0.0, 0.0, 0.0};
-                    for (int w = 0; w < 8; ++w) {
-                        finish3<MODE>(red[w][0], red[w][1], red[w][2], redd[w], P.nq, v);
-                        tot[0] += v[0]; tot[1] += v[1]; tot[2] += v[2];
-                    }
+                if (lane == 0) {
+                    double v[3];
+                    finish3<MODE>(q, s1, u, qd, P.nq, v);
                     if (P.per_a) {
-                        double* o = P.out + ((size_t)i * TILES + tile) * 3;
-                        o[0] = tot[0]; o[1] = tot[1]; o[2] = tot[2];
+                        double* o = P.out + (((size_t)i * TILES + tile) * 8 + warp) * 3;
+                        o[0] = v[0]; o[1] = v[1]; o[2] = v[2];
                     } else {
-                        acc[0] += tot[0]; acc[1] += tot[1]; acc[2] += tot[2];
+                        accw[0] += v[0]; accw[1] += v[1]; accw[2] += v[2];
                     }
                 }
-                __syncthreads();  // red[] is reused by the next tile
             }
             __syncthreads();
             if (tid == 0) red_release_add(P.done2 + slot, 1u);
         }
     }
-    if (!P.per_a && tid == 0) {
-        P.out[blockIdx.x * 3 + 0] = acc[0];
-        P.out[blockIdx.x * 3 + 1] = acc[1];
-        P.out[blockIdx.x * 3 + 2] = acc[2];
+    if (!P.per_a) {
+        // fixed-order combination of the 8 warps' FP64 sums
+        if (lane == 0) { red64[warp][0] = accw[0]; red64[warp][1] = accw[1]; red64[warp][2] = accw[2]; }
+        __syncthreads();
+        if (tid == 0) {
+            double s0 = 0.0, s1 = 0.0, s2 = 0.0;
+            for (int w = 0; w < 8; ++w) { s0 += red64[w][0]; s1 += red64[w][1]; s2 += red64[w][2]; }
+            P.out[blockIdx.x * 3 + 0] = s0;
+            P.out[blockIdx.x * 3 + 1] = s1;
+            P.out[blockIdx.x * 3 + 2] = s2;
+        }
     }
 }
 
@@ -318,11 +365,13 @@ static cudaError_t launch_onepass_m(OnepassArgs& A, int sm_count, cudaStream_t s
     }
 }
 
+// exchange buffers (pass 1: 8 warps x 2^10 values; pass 2: one 2^13 tile), plus the pass-1
+// row staging for K1 = 10
 template <int K1, int M>
 static constexpr size_t twopass_smem() {
-    return (K1 == 10 ? 8 * tile_slots(10) : tile_slots(13)) * sizeof(float2) > tile_slots(13) * sizeof(float2)
-               ? 8 * tile_slots(10) * sizeof(float2)
-               : tile_slots(13) * sizeof(float2);
+    return ((K1 == 10 ? 8 * tile_slots(10) : tile_slots(13)) > tile_slots(13) ? 8 * tile_slots(10) : tile_slots(13)) *
+               sizeof(float2) +
+           (K1 == 10 ? kStageSlots * sizeof(float2) : 0);
 }
 
 template <int K1, int M, int MODE>

@@ -44,8 +44,12 @@ def test_reference_arm_only_rank0_prints():
 
 
 def test_roofline_helpers(tmp_path, monkeypatch):
-    assert bench.ops_per_string(20) == 24 and bench.ops_per_string(22) == 26
+    # algorithmic counts per unit: N + 7 FP32 ops per Pauli string, 16 N tensor FLOPs per Pauli
+    # string, 4.7 N + 8 FP32 ops per mana point
+    assert bench.ops_per_string(20) == 27 and bench.ops_per_string(22) == 29
     assert bench.tensor_flops_per_string(22) == 4 * (128 + 64 + 128)
+    assert bench.tensor_alg_flops_per_string(22) == 352
+    assert bench.mana_ops_per_point(11) == pytest.approx(59.7)
     assert bench.fp32_peak_ops(152, 2070.0) == pytest.approx(152 * 128 * 2.07e9)
     assert bench.aggregate_rate(4, 5, 1e9, 2.0) == pytest.approx(1e10)
     assert bench.max_over_ranks(1.5, 1) == 1.5
