@@ -416,7 +416,10 @@ def main():
                        "parallelism": (f"X-strings split over {world} ranks (chunk-aligned slices, NCCL all-gather "
                                        "of per-chunk FP64 sums)") if sharded else "one state per GPU",
                        "l2": f"state ({psi_np.nbytes >> 20} MiB) is smaller than L2: a 256 MiB buffer is written between steps",
-                       "M2": M, "lost_norm": ln},
+                       "M2": M, "lost_norm": ln,
+                       "twopass_shape": (dict(zip(("units_per_pass1_warp", "tiles_per_pass2_task", "ring_slots",
+                                                   "xstrings_per_batch"), ctx.twopass_shape(N, 2.0)))
+                                         if 16 <= N <= 24 else None)},
             "roofline": roof,
             "clocks": clocks,
             "gpu_launches": launches,
@@ -551,10 +554,11 @@ def metric_lines(hm, dev, sm_count, flush, reps: int = 3, frac_log2: int = 3):
     return out
 
 
-NEW_ROWS = ("ti_N20_L10", "mana_mixed_N8_of_10", "sre_even_sector_N20_u1", "mana_qudit_d5_N6", "mana_grad_d3_N9")
+NEW_ROWS = ("batched_64_fwd_bwd", "ti_N20_L10", "mana_mixed_N8_of_10", "sre_even_sector_N20_u1", "mana_qudit_d5_N6",
+            "mana_grad_d3_N9")
 
 
-def new_rows_in_child(timeout_s: float = 300.0):
+def new_rows_in_child(timeout_s: float = 480.0):
     """Times the Algorithm 3 / Algorithm 6, even-sector, qudit and mana-gradient workloads (the
     --extra lines of those rows) in a separate process, after the headline measurement: a CUDA
     error there cannot reach the headline's context, and a time limit bounds it."""
@@ -638,12 +642,19 @@ def extra_workloads(hm, dev, sm_count, only: str = ""):
                 "hbm_state_reads_GBps": 4097 * 2 * psi.numel() * 8 / dt / 1e9}
     guard("mc_N28", mc28)
 
-    # batched forward + backward: 64 states, N uniform in 10..18, one persistent launch
+    # batched forward + backward: 64 states, N uniform in 10..18, one persistent launch, against
+    # a loop of single-state calls over the same states (forward + backward, and forward only)
     def batched():
         Ns, states = inputs.batched_ladder_states(64, 10, 18, 8, seed=4001)
         ts = [torch.from_numpy(x).to(dev) for x in states]
+        strings = sum(4.0 ** n for n in Ns)
         dt, _ = timed(lambda: hm.sre_batched(ts, want_grad=True), reps=2)
-        return {"strings_per_s": sum(4.0 ** n for n in Ns) / dt, "s": dt, "states": len(Ns)}
+        dl, _ = timed(lambda: [hm.sre_grad(t) for t in ts], reps=2)
+        df, _ = timed(lambda: hm.sre_batched(ts, want_grad=False), reps=2)
+        dlf, _ = timed(lambda: [hm.sre(t, 2.0) for t in ts], reps=2)
+        return {"strings_per_s": strings / dt, "s": dt, "states": len(Ns),
+                "loop_fwd_bwd_s": dl, "speedup_over_loop": dl / dt,
+                "fwd_only_s": df, "loop_fwd_only_s": dlf, "fwd_speedup_over_loop": dlf / df}
     guard("batched_64_fwd_bwd", batched)
 
     # thermodynamic-integration M2 (Algorithm 3) on the N = 20 brickwork state: L = 10 chains,

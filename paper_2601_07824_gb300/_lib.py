@@ -28,7 +28,7 @@ EXPORTS = [
     "hadamag_reduced_density_matrix", "hadamag_sre_even_sector", "hadamag_mana_qudit", "hadamag_mana_grad",
     "hadamag_mana_mixed_qudit", "hadamag_reduced_density_matrix_qudit", "hadamag_set_fp32_powers",
     "hadamag_sre_chunk", "hadamag_sre_slice", "hadamag_sre_combine", "hadamag_sre_grad_slice",
-    "hadamag_sre_grad_combine",
+    "hadamag_sre_grad_combine", "hadamag_set_autotune", "hadamag_twopass_shape", "hadamag_set_twopass_shape",
 ]
 
 
@@ -87,6 +87,9 @@ def load(path: str | None = None):
             "hadamag_mana_mixed": [V, V, I, I, PD, PD, V],
             "hadamag_reduced_density_matrix": [V, V, I, I, ctypes.POINTER(I), I, V, V],
             "hadamag_sre_chunk": [I],
+            "hadamag_set_autotune": [V, I],
+            "hadamag_twopass_shape": [V, I, D, ctypes.POINTER(I)],
+            "hadamag_set_twopass_shape": [V, I, D, I, I, I],
             "hadamag_sre_slice": [V, V, I, D, I, L, L, V, V],
             "hadamag_sre_combine": [I, D, PD, L, PD, PD],
             "hadamag_sre_grad_slice": [V, V, I, I, L, L, PD, V, V],
@@ -145,6 +148,22 @@ class Context:
     def set_fp32_powers(self, on: bool):
         """Opt into FP32 powers for non-integer n (see hadamag_set_fp32_powers)."""
         self.check(self.lib.hadamag_set_fp32_powers(self.h, 1 if on else 0), "hadamag_set_fp32_powers")
+
+    def set_autotune(self, on: bool):
+        """Launch-shape autotuning on (default) or off (see hadamag_set_autotune)."""
+        self.check(self.lib.hadamag_set_autotune(self.h, 1 if on else 0), "hadamag_set_autotune")
+
+    def twopass_shape(self, N: int, n: float = 2.0):
+        """[units per pass-1 warp, tiles per pass-2 task, ring slots, X-strings per batch] in use
+        for (N, n); zeros before the tuner ran."""
+        out = (ctypes.c_int * 4)()
+        self.check(self.lib.hadamag_twopass_shape(self.h, int(N), float(n), out), "hadamag_twopass_shape")
+        return list(out)
+
+    def set_twopass_shape(self, N: int, n: float, upw: int, tpt: int, R: int = 0):
+        """Pin the two-pass shape for (N, n) (see hadamag_set_twopass_shape)."""
+        self.check(self.lib.hadamag_set_twopass_shape(self.h, int(N), float(n), int(upw), int(tpt), int(R)),
+                   "hadamag_set_twopass_shape")
 
     def set_wait_limit(self, spins: int, bias: int = 0):
         self.check(self.lib.hadamag_set_wait_limit(self.h, int(spins), int(bias)), "hadamag_set_wait_limit")

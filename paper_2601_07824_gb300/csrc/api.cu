@@ -86,7 +86,9 @@ hadamag_status as_c64(hadamag_ctx_t c, const void* psi, int64_t n, hadamag_dtype
 
 int sre_mode(double n) { return n == 1.0 ? 1 : n == 2.0 ? 2 : n == 3.0 ? 3 : 0; }
 
-TwoPlan plan_twopass(int N) {
+// Two-pass launch shape for N: X-strings per batch A, ring slots R (0: the default), units per
+// pass-1 warp UPW (K1 = 10) and column tiles per pass-2 task TPT.
+TwoPlan plan_twopass(int N, int UPW, int TPT, int R) {
     TwoPlan p{};
     const int L = N - 1, K1 = twopass_k1(N), M = L - K1;
     const size_t per_a = ((size_t)1 << L) * sizeof(float2);
@@ -101,12 +103,15 @@ TwoPlan plan_twopass(int N) {
         p.R = (N <= 22) ? 4 : 2;
     }
     p.A = A;
+    if (R > 0) p.R = R;
     p.tiles = twopass_tiles_per_a(N);
     p.triples = twopass_triples_per_a(N);
-    // a pass-1 task covers A X-strings x (U or 1) units per warp x 2 units (K1 = 10);
-    // a pass-2 task covers two adjacent column tiles
-    p.p1 = (K1 == 10) ? (1 << M) / (p.U * 2) : (1 << M);
-    p.p2 = A * p.tiles / 2;
+    p.UPW = (K1 == 10) ? UPW : 1;
+    p.TPT = TPT;
+    // a pass-1 task covers A X-strings x (U or 1) warps x UPW units per warp (K1 = 10), or one
+    // unit (K1 = 13); a pass-2 task covers TPT adjacent column tiles
+    p.p1 = (K1 == 10) ? (1 << M) / (p.U * p.UPW) : (1 << M);
+    p.p2 = A * p.tiles / p.TPT;
     p.scratch_bytes = (size_t)p.R * A * per_a;
     return p;
 }
@@ -120,7 +125,8 @@ hadamag_status run_sre(hadamag_ctx_t c, const float2* psi, int N, double n, int6
     if (mode == 0 && c->fp32_powers && n <= 4.0 && n * (N + 2) <= 100.0) mode = 4;
     hadamag_status s;
     cudaError_t e;
-    if (N <= 15) {
+    if (N == 15 && (s = tune_twopass(c, psi, N, n, mode, st))) return s;
+    if (N < 15 || (N == 15 && !c->twopass_shape[N][mode].UPW)) {
         OnepassArgs A{};
         A.psi = psi; A.N = N; A.nq = n; A.count = count; A.a_list = a_list;
         A.per_a = per_a; A.status = (int*)c->status.ptr; A.grid = 0;
@@ -139,14 +145,26 @@ hadamag_status run_sre(hadamag_ctx_t c, const float2* psi, int N, double n, int6
         return HADAMAG_OK;
     }
     if (N > 24) return fail(c, HADAMAG_ERR_UNSUPPORTED, "exact SRE supports N <= 24 (got %d)", N);
-    TwoPlan pl = plan_twopass(N);
+    if ((s = tune_twopass(c, psi, N, n, mode, st))) return s;
+    const TwoShape& sh = c->twopass_shape[N][mode];
+    TwoPlan pl = sh.UPW ? plan_twopass(N, sh.UPW, sh.TPT, sh.R) : plan_twopass(N);
+    return launch_twopass_plan(c, psi, N, n, mode, pl, count, a_list, 0, per_a, terms, st, nparts);
+}
+
+// One two-pass launch with plan `pl` (X-strings a_list[i], or a_base + i without a list).
+hadamag_status launch_twopass_plan(hadamag_ctx_t c, const float2* psi, int N, double n, int mode, const TwoPlan& pl,
+                                   int64_t count, const int64_t* a_list, int64_t a_base, int per_a, double* terms,
+                                   cudaStream_t st, int64_t* nparts) {
+    hadamag_status s;
+    cudaError_t e;
     int grid = 0;
     if ((e = twopass_max_grid(N, mode, c->sm_count, &grid)) != cudaSuccess) return cuda_fail(c, e, "occupancy");
     if ((s = ensure_buf(c, c->scratch, pl.scratch_bytes))) return s;
     if ((s = ensure_buf(c, c->counters, 2 * 64 * sizeof(unsigned)))) return s;
     TwoPassParams P{};
-    P.psi = psi; P.N = N; P.nq = n; P.count = count; P.a_list = a_list;
+    P.psi = psi; P.N = N; P.nq = n; P.count = count; P.a_list = a_list; P.a_base = a_base;
     P.scratch = (float2*)c->scratch.ptr; P.R = pl.R; P.A = pl.A; P.U = pl.U;
+    P.UPW = pl.UPW; P.TPT = pl.TPT;
     P.n_batches = (count + pl.A - 1) / pl.A;
     P.p1 = pl.p1; P.p2 = pl.p2;
     P.done1 = (unsigned*)c->counters.ptr; P.done2 = P.done1 + 64;
@@ -174,6 +192,88 @@ hadamag_status run_sre(hadamag_ctx_t c, const float2* psi, int N, double n, int6
     }
     if (nparts) *nparts = grid;
     return HADAMAG_OK;
+}
+
+// The two-pass autotuner: on the first uncaptured call for (N, mode) it times each candidate
+// task shape on a bounded range of X-strings (a >= 2^(N-1), the common kind; two launches each,
+// the second timed with CUDA events on the call's stream) and keeps the fastest for the context.
+// Candidates: units per pass-1 warp {2, 4} (K1 = 10) x tiles per pass-2 task {2, 4}, and for
+// N = 20 also 3 or 4 ring slots.  At N = 15 the split itself is tuned: the one-pass kernel (the
+// whole 2^14-value transform in one CTA's shared memory) against two passes through L2 (10 + 4
+// bits; tiles per pass-2 task {1, 2}).  Under stream capture, or with autotuning off, the
+// defaults run (one pass at N = 15).
+hadamag_status tune_twopass(hadamag_ctx_t c, const float2* psi, int N, double n, int mode, cudaStream_t st) {
+    TwoShape& sh = c->twopass_shape[N][mode];
+    if (sh.UPW || sh.onepass || !c->autotune) return HADAMAG_OK;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e;
+    if ((e = cudaStreamIsCapturing(st, &cap)) != cudaSuccess) return cuda_fail(c, e, "capture query");
+    if (cap != cudaStreamCaptureStatusNone) return HADAMAG_OK;
+    struct Cand { int UPW, TPT, R; };  // UPW 0: the one-pass kernel (N = 15)
+    Cand cands[16];
+    int nc = 0;
+    const bool k10 = twopass_k1(N) == 10;
+    if (N == 15) cands[nc++] = {0, 0, 0};
+    for (int upw : {2, 4}) {
+        if (!k10 && upw != 2) continue;
+        for (int tpt : {1, 2, 4}) {
+            if (tpt > twopass_tiles_per_a(N) || (tpt == 1 && N != 15)) continue;
+            if (N == 20) { cands[nc++] = {upw, tpt, 3}; cands[nc++] = {upw, tpt, 4}; }
+            else cands[nc++] = {upw, tpt, 0};
+        }
+    }
+    const int64_t cnt = int64_t(1) << (N <= 20 ? 13 : 10);
+    const int64_t base = int64_t(1) << (N - 1);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return fail(c, HADAMAG_ERR_CUDA, "events");
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return fail(c, HADAMAG_ERR_CUDA, "events"); }
+    float best = 1e30f;
+    Cand win = cands[0];
+    hadamag_status s = HADAMAG_OK;
+    for (int k = 0; k < nc && !s; ++k) {
+        const TwoPlan pl = cands[k].UPW ? plan_twopass(N, cands[k].UPW, cands[k].TPT, cands[k].R) : TwoPlan{};
+        for (int rep = 0; rep < 2 && !s; ++rep) {
+            if (rep == 1) cudaEventRecord(e0, st);
+            int64_t np = 0;
+            if (cands[k].UPW) {
+                s = launch_twopass_plan(c, psi, N, n, mode, pl, cnt, nullptr, base, 0, nullptr, st, &np);
+            } else {
+                OnepassArgs A{};
+                A.psi = psi; A.N = N; A.nq = n; A.count = cnt; A.a_list = nullptr; A.a_base = base;
+                A.per_a = 0; A.status = (int*)c->status.ptr;
+                const int64_t maxgrid = (int64_t)c->sm_count * 64;
+                if ((s = ensure_buf(c, c->part, (size_t)maxgrid * 3 * sizeof(double)))) break;
+                A.out = (double*)c->part.ptr;
+                A.grid = (int)maxgrid;
+                if ((e = launch_onepass(A, mode, c->sm_count, st)) != cudaSuccess) s = cuda_fail(c, e, "sre_onepass");
+                c->launches++;
+            }
+            if (rep == 1) cudaEventRecord(e1, st);
+        }
+        if (s) break;
+        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) { s = cuda_fail(c, e, "tune sync"); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; win = cands[k]; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (s) return s;
+    if ((s = status_word_now(c, st))) return s;
+    sh.UPW = win.UPW;
+    sh.TPT = win.TPT;
+    sh.R = win.R;
+    sh.onepass = win.UPW == 0;
+    return HADAMAG_OK;
+}
+
+// Reads the device status word (synchronising `st`) without clearing it.
+hadamag_status status_word_now(hadamag_ctx_t c, cudaStream_t st) {
+    cudaError_t e;
+    if ((e = cudaMemcpyAsync(c->host_status, c->status.ptr, sizeof(int), cudaMemcpyDeviceToHost, st)) != cudaSuccess)
+        return cuda_fail(c, e, "copy status");
+    if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return cuda_fail(c, e, "stream sync");
+    return status_word(c);
 }
 
 hadamag_status begin(hadamag_ctx_t c, cudaStream_t st) {
@@ -268,6 +368,50 @@ extern "C" hadamag_status hadamag_set_wait_limit(hadamag_ctx_t c, long long spin
     if (!c || spins < 1) return HADAMAG_ERR_INVALID_ARG;
     c->spin_limit = spins;
     c->wait_bias = bias;
+    return HADAMAG_OK;
+}
+
+extern "C" hadamag_status hadamag_set_autotune(hadamag_ctx_t c, int on) {
+    if (!c || (on != 0 && on != 1)) return HADAMAG_ERR_INVALID_ARG;
+    c->autotune = on;
+    return HADAMAG_OK;
+}
+
+extern "C" hadamag_status hadamag_twopass_shape(hadamag_ctx_t c, int N, double n, int* out4) {
+    if (!c || !out4 || N < 15 || N > 24 || !(n > 0.0)) return HADAMAG_ERR_INVALID_ARG;
+    int mode = sre_mode(n);
+    if (mode == 0 && c->fp32_powers && n <= 4.0 && n * (N + 2) <= 100.0) mode = 4;
+    const TwoShape& sh = c->twopass_shape[N][mode];
+    if (sh.onepass) {
+        out4[0] = out4[1] = out4[2] = out4[3] = -1;
+        return HADAMAG_OK;
+    }
+    const TwoPlan pl = sh.UPW ? plan_twopass(N, sh.UPW, sh.TPT, sh.R) : plan_twopass(N);
+    out4[0] = sh.UPW ? pl.UPW : 0;
+    out4[1] = sh.UPW ? pl.TPT : 0;
+    out4[2] = sh.UPW ? pl.R : 0;
+    out4[3] = sh.UPW ? pl.A : 0;
+    return HADAMAG_OK;
+}
+
+extern "C" hadamag_status hadamag_set_twopass_shape(hadamag_ctx_t c, int N, double n, int upw, int tpt, int R) {
+    if (!c || N < 15 || N > 24 || !(n > 0.0)) return HADAMAG_ERR_INVALID_ARG;
+    int mode = sre_mode(n);
+    if (mode == 0 && c->fp32_powers && n <= 4.0 && n * (N + 2) <= 100.0) mode = 4;
+    TwoShape& sh = c->twopass_shape[N][mode];
+    if (upw == -1 && N == 15) {  // the one-pass kernel
+        sh = TwoShape{};
+        sh.onepass = 1;
+        return HADAMAG_OK;
+    }
+    const bool k10 = twopass_k1(N) == 10;
+    if ((k10 ? (upw != 2 && upw != 4) : upw != 2) || tpt < 1 || tpt > twopass_tiles_per_a(N) ||
+        (twopass_tiles_per_a(N) % tpt) || !(R == 0 || (R >= 2 && R <= 4)))
+        return HADAMAG_ERR_INVALID_ARG;
+    sh.UPW = upw;
+    sh.TPT = tpt;
+    sh.R = R;
+    sh.onepass = 0;
     return HADAMAG_OK;
 }
 

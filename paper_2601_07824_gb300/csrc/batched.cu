@@ -5,9 +5,11 @@
 //     with the one-pass adjoint (grad_phases.cuh), a private partial gradient per thread group,
 //     then the CTA reduces the partials in a fixed order and writes dM_2/dpsi* and M_2;
 //   * large states (15 <= N <= 18): the three passes of the adjoint (pass 1/2/3 tasks in stage
-//     order, runtime dispatch on M = N - 11), scattering into per-CTA partial gradients shared by
-//     all large states, followed by finalize tasks that reduce those partials (FP64, fixed CTA
-//     order), write the gradient, zero the partials and release them to the next large state.
+//     order, runtime dispatch on M = N - 11), scattering into per-CTA partial gradients, followed
+//     by finalize tasks that reduce those partials (FP64, fixed CTA order), write the gradient
+//     and zero the partials.  Each large state has its own set of partials (a buffer slot) unless
+//     the states would need more memory than the host's budget allows; then states take turns on
+//     the slots, a state's pass 3 waiting for the finalize of the previous state on its slot.
 // Forward only (no gradient requested): small states skip the cube, the back transform and the
 // scatter; large states run passes 1 and 2 only, and one finalize task per state turns the
 // pass-2 sums into M_2 once every pass-2 task has counted in.  No partial-gradient buffers.
@@ -19,8 +21,10 @@
 
 namespace hm {
 
+// The task functions are not inlined: each gets its own register allocation under the
+// kernel's 128-register cap (inlined into one loop they needed ~245 and spilled ~1.2 KB).
 template <int L, bool FWD>
-__device__ __forceinline__ void small_item(const BatchState& s, float2* smem, double* m2_out, int idx) {
+__device__ __noinline__ void small_item(const BatchState& s, float2* smem, double* m2_out, int idx) {
     constexpr int G = OnepassShape<L>::G, GPC = 256 / G;  // groups of one 256-thread CTA
     static_assert(L >= 9 && L <= 13, "small items cover N = 10..14");
     __shared__ double sums[GPC][2];
@@ -67,7 +71,7 @@ __device__ __forceinline__ bool large_task_fwd(const BatchState& s, const G3Ctl&
 }
 
 template <int M>
-__device__ __forceinline__ bool large_task(const BatchedParams& B, const BatchState& s, int64_t local, float2* smem) {
+__device__ __noinline__ bool large_task(const BatchedParams& B, const BatchState& s, int64_t local, float2* smem) {
     if (s.fwd) return large_task_fwd<M>(s, B.ctl, local, smem);
     const G3State S{s.psi, s.N, s.scratch, s.R, s.A, s.U, s.n_batches, s.p1, s.p2, s.p3,
                     s.ctr, s.ctr + 64, s.ctr + 128};
@@ -87,10 +91,10 @@ __device__ __forceinline__ bool large_task(const BatchedParams& B, const BatchSt
     }
     // pass 3 writes the shared partials: the previous large state must have released them
     const unsigned* prev = s.prev_fin;
-    return g3_pass3<M>(S, B.ctl, g, r, smem, B.gpart + (size_t)blockIdx.x * B.dimmax, prev, prev ? s.prev_nfin : 0u);
+    return g3_pass3<M>(S, B.ctl, g, r, smem, s.gpart + ((size_t)blockIdx.x << s.N), prev, prev ? s.prev_nfin : 0u);
 }
 
-__device__ __forceinline__ bool finalize_task(const BatchedParams& B, const BatchState& s, int f, double* m2_out,
+__device__ __noinline__ bool finalize_task(const BatchedParams& B, const BatchState& s, int f, double* m2_out,
                                               int idx) {
     if (s.fwd) {
         // forward only: every pass-2 task has added its sums into s2
@@ -120,7 +124,7 @@ __device__ __forceinline__ bool finalize_task(const BatchedParams& B, const Batc
     for (int64_t z = z0 + threadIdx.x; z < z1; z += blockDim.x) {
         double gx = 0.0, gy = 0.0;
         for (int k = 0; k < B.nparts; ++k) {
-            float2* p = B.gpart + (size_t)k * B.dimmax + z;
+            float2* p = s.gpart + ((size_t)k << s.N) + z;
             const float2 v = __ldcg(p);
             gx += v.x;
             gy += v.y;
@@ -144,8 +148,14 @@ __global__ void __launch_bounds__(256, 2) batched_kernel(BatchedParams B) {
         const int64_t tau = s_ticket;
         __syncthreads();
         if (tau >= B.total) break;
-        int idx = 0;
-        while (idx + 1 < B.n_states && B.states[idx + 1].task_begin <= tau) ++idx;
+        // the state whose ticket segment holds tau (segments are contiguous, in state order)
+        int lo = 0, hi = B.n_states - 1;
+        while (lo < hi) {
+            const int mid = (lo + hi + 1) >> 1;
+            if (B.states[mid].task_begin <= tau) lo = mid;
+            else hi = mid - 1;
+        }
+        const int idx = lo;
         const BatchState& s = B.states[idx];
         const int64_t local = tau - s.task_begin;
         bool ok = true;
@@ -178,7 +188,7 @@ __global__ void __launch_bounds__(256, 2) batched_kernel(BatchedParams B) {
     }
 }
 
-size_t batched_smem_bytes() { return (size_t)tile_slots(13) * sizeof(float2); }
+size_t batched_smem_bytes() { return (size_t)(tile_slots(13) + kStageSlots) * sizeof(float2); }
 
 cudaError_t batched_max_grid(int sm_count, int* grid) {
     cudaError_t e = cudaFuncSetAttribute(batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,

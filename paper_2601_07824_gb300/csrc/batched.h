@@ -26,7 +26,8 @@ struct BatchState {
     int n_fin;                 // finalize tasks
     unsigned* ctr;             // [64 done1][64 done2][64 done3], zeroed before launch
     unsigned* fin;             // finalize tasks done (zeroed)
-    const unsigned* prev_fin;  // previous large state's fin counter, or null
+    float2* gpart;             // this state's per-CTA partial gradients [nparts][2^N] (a buffer slot)
+    const unsigned* prev_fin;  // fin counter of the previous large state on the same slot, or null
     unsigned prev_nfin;
     double* s2;                // [S_2, S_1] accumulated with atomics (zeroed)
 };
@@ -36,9 +37,7 @@ struct BatchedParams {
     int n_states;
     int64_t total;             // total tickets
     unsigned long long* ticket;
-    float2* gpart;             // per-CTA partial gradients [nparts][dimmax], zero on entry and exit
-    int64_t dimmax;
-    int nparts;                // = grid
+    int nparts;                // = grid; partial-gradient buffers are zero on entry and exit
     double* m2_out;            // [n_states] (device)
     G3Ctl ctl;
 };

@@ -17,6 +17,10 @@ using namespace hm;
 
 namespace {
 
+// Device memory the per-CTA partial gradients of the large states may take (one slot each
+// while they fit).
+constexpr size_t kPartBudget = (size_t)16 << 30;
+
 struct Plan {
     std::vector<BatchState> st;
     int64_t total = 0;
@@ -108,7 +112,14 @@ hadamag_status run(hadamag_ctx_t c, int count, const void* const* psi, const int
     if ((s = ensure_buf(c, c->batch_meta, meta_bytes))) return s;
     if ((s = ensure_buf(c, c->scratch, std::max<size_t>(p.scratch_bytes, 256)))) return s;
     if ((s = ensure_buf(c, c->batch_sums, std::max<size_t>(p.gsmall_bytes, 256)))) return s;
-    const size_t gpart_bytes = (p.n_large && want_grad) ? (size_t)grid * p.dimmax * sizeof(float2) : 256;
+    // partial-gradient buffer slots: one per large state while they fit kPartBudget, else fewer
+    // slots taken in turn (slot = large-state index mod slots)
+    const size_t slot_bytes = (size_t)grid * p.dimmax * sizeof(float2);
+    int slots = 0;
+    if (p.n_large && want_grad) {
+        slots = (int)std::min<size_t>((size_t)p.n_large, std::max<size_t>(1, kPartBudget / slot_bytes));
+    }
+    const size_t gpart_bytes = slots ? (size_t)slots * slot_bytes : 256;
     if ((s = ensure_buf(c, c->grad_acc, gpart_bytes))) return s;
     if (c->host_table_bytes < table_bytes) {
         if (c->host_table) cudaFreeHost(c->host_table);
@@ -122,8 +133,9 @@ hadamag_status run(hadamag_ctx_t c, int count, const void* const* psi, const int
     double* s2 = (double*)(meta + table_bytes + ctr_bytes);
     unsigned long long* ticket = (unsigned long long*)(meta + table_bytes + ctr_bytes + s2_bytes);
     size_t soff = 0, goff = 0;
-    const unsigned* prev_fin = nullptr;
-    unsigned prev_nfin = 0;
+    std::vector<const unsigned*> slot_fin(slots > 0 ? slots : 1, nullptr);
+    std::vector<unsigned> slot_nfin(slots > 0 ? slots : 1, 0u);
+    int li = 0;  // large-state index
     for (int k = 0; k < ns; ++k) {
         BatchState& b = p.st[k];
         b.ctr = ctr + (size_t)k * 256;
@@ -137,10 +149,15 @@ hadamag_status run(hadamag_ctx_t c, int count, const void* const* psi, const int
         } else {
             b.scratch = (float2*)((char*)c->scratch.ptr + soff);
             soff += (size_t)b.R * b.A * ((size_t)1 << (b.N - 1)) * sizeof(float2);
-            b.prev_fin = prev_fin;
-            b.prev_nfin = prev_nfin;
-            prev_fin = b.fin;
-            prev_nfin = (unsigned)b.n_fin;
+            if (slots) {
+                const int sl = li % slots;
+                b.gpart = (float2*)((char*)c->grad_acc.ptr + (size_t)sl * slot_bytes);
+                b.prev_fin = slot_fin[sl];
+                b.prev_nfin = slot_nfin[sl];
+                slot_fin[sl] = b.fin;
+                slot_nfin[sl] = (unsigned)b.n_fin;
+            }
+            ++li;
         }
     }
     std::memcpy(c->host_table, p.st.data(), table_bytes);
@@ -156,8 +173,6 @@ hadamag_status run(hadamag_ctx_t c, int count, const void* const* psi, const int
     B.n_states = ns;
     B.total = p.total;
     B.ticket = ticket;
-    B.gpart = (float2*)c->grad_acc.ptr;
-    B.dimmax = p.dimmax;
     B.nparts = grid;
     B.m2_out = m2;
     B.ctl = G3Ctl{(int*)c->status.ptr, c->spin_limit, c->wait_bias};

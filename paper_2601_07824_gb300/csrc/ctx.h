@@ -18,7 +18,14 @@ struct DevBuf {
 
 struct TwoPlan {
     int A, U, R, p1, p2, tiles, triples;  // triples: per-X-string output triples (per_a)
+    int UPW, TPT;                         // task shapes: units per pass-1 warp, tiles per pass-2 task
     size_t scratch_bytes;
+};
+
+// Two-pass task shapes picked by the context's autotuner for one (N, accumulation mode).
+struct TwoShape {
+    int UPW = 0, TPT = 0, R = 0;  // 0: not tuned yet
+    int onepass = 0;              // N = 15: 1 when the one-pass kernel won
 };
 
 }  // namespace hm
@@ -35,6 +42,7 @@ struct hadamag_ctx_s {
     long long spin_limit = hm::kDefaultSpinLimit;
     unsigned wait_bias = 0;
     int autotune = 1;
+    hm::TwoShape twopass_shape[25][5];  // [N][mode], filled by the two-pass autotuner
     int fp32_powers = 0;  // non-integer n: FP32 powers (mode 4) where n <= 4 and n (N + 2) <= 100
     void* host_table = nullptr;  // pinned copy of the batched state table
     size_t host_table_bytes = 0;
@@ -55,9 +63,14 @@ bool aligned16(const void* p);
 hadamag_status as_c64(hadamag_ctx_t c, const void* psi, int64_t n, hadamag_dtype dt, cudaStream_t st,
                       const float2** out);
 int sre_mode(double n);
-TwoPlan plan_twopass(int N);
+TwoPlan plan_twopass(int N, int UPW = 2, int TPT = 2, int R = 0);
 hadamag_status run_sre(hadamag_ctx_t c, const float2* psi, int N, double n, int64_t count,
                        const int64_t* a_list, int per_a, double* terms, cudaStream_t st, int64_t* nparts);
+hadamag_status launch_twopass_plan(hadamag_ctx_t c, const float2* psi, int N, double n, int mode, const TwoPlan& pl,
+                                   int64_t count, const int64_t* a_list, int64_t a_base, int per_a, double* terms,
+                                   cudaStream_t st, int64_t* nparts);
+hadamag_status tune_twopass(hadamag_ctx_t c, const float2* psi, int N, double n, int mode, cudaStream_t st);
+hadamag_status status_word_now(hadamag_ctx_t c, cudaStream_t st);
 hadamag_status begin(hadamag_ctx_t c, cudaStream_t st);
 hadamag_status finish(hadamag_ctx_t c, const double* res_dev, int n, cudaStream_t st);
 hadamag_status status_word(hadamag_ctx_t c);

@@ -74,9 +74,15 @@ __global__ void __launch_bounds__(256, 2) grad_threepass(GradParams P) {
         else ok = g3_pass3<M>(S, C, g, r, smem, gp);
         if (!ok) return;
     }
+    // the 8 warps' sums (lane 0 of each), combined in a fixed order
+    __shared__ double red[8][2];
+    if ((tid & 31) == 0) { red[tid >> 5][0] = acc; red[tid >> 5][1] = acc1; }
+    __syncthreads();
     if (tid == 0) {
-        P.sums[blockIdx.x * 3 + 0] = acc;
-        P.sums[blockIdx.x * 3 + 1] = acc1;
+        double t0 = 0.0, t1 = 0.0;
+        for (int w = 0; w < 8; ++w) { t0 += red[w][0]; t1 += red[w][1]; }
+        P.sums[blockIdx.x * 3 + 0] = t0;
+        P.sums[blockIdx.x * 3 + 1] = t1;
         P.sums[blockIdx.x * 3 + 2] = 0.0;
     }
 }
@@ -166,7 +172,8 @@ cudaError_t launch_grad_onepass(const float2* psi, int N, double* sums, float2* 
     }
 }
 
-static constexpr size_t kGradSmem = tile_slots(13) * sizeof(float2);
+// pass-2/3 exchange (one 2^13 tile; pass 1: 8 warps x 2^10) plus the pass-1 row staging
+static constexpr size_t kGradSmem = (tile_slots(13) + kStageSlots) * sizeof(float2);
 
 template <int M>
 static cudaError_t grad3_prep(int* occ) {

@@ -37,8 +37,7 @@ hadamag_status enqueue_grad_parts(hadamag_ctx_t c, const float2* p, int N, int64
         GradParams P{};
         const int M = N - 11;
         const size_t per_a = (size_t)dim / 2 * sizeof(float2);
-        int A = 8;
-        while (A > 1 && (size_t)A * per_a > ((size_t)16 << 20)) A >>= 1;
+        const int A = 8;  // the 8 pass-1 warps share the state rows of two units (staged once)
         P.psi = p; P.N = N; P.R = 3; P.A = A; P.U = 8 / A;
         P.n_batches = count / A;
         P.a_base = a0;

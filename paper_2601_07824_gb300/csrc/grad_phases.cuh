@@ -68,6 +68,13 @@ __device__ __forceinline__ bool g3_pass1(const G3State& S, const G3Ctl& C, int64
     const int64_t unit = ((int64_t)r * S.U + warp / S.A) * 2;
     const int64_t a = S.a_base + g * S.A + a_idx;
     const int64_t dim = int64_t(1) << S.N;
+    // with 8 X-strings per batch (U == 1) the CTA's warps read the same state rows (consecutive
+    // aligned X-strings): stage them once in shared memory (the caller reserves kStageSlots
+    // values after the 8 warps' exchange buffers)
+    const int64_t a0 = S.a_base + g * S.A;
+    const bool stage = S.U == 1 && a0 < dim;  // CTA-uniform
+    float2* rows = smem + 8 * tile_slots(10);
+    if (stage) stage_rows<M>(rows, S.psi, a0, unit);
     if (a < dim) {
         float2* sbase = S.scratch + (size_t)slot * S.A * ((size_t)1 << L);
         float2* sm = smem + warp * tile_slots(10);
@@ -75,8 +82,14 @@ __device__ __forceinline__ bool g3_pass1(const G3State& S, const G3Ctl& C, int64
         for (int uu = 0; uu < 2; ++uu) {
             const PairRows<K1, M> pr(a, unit + uu);
             float2* dst = sbase + (size_t)a_idx * ((size_t)1 << L) + ((size_t)(unit + uu) << K1);
+            if (stage) {
+                const float2* rw = rows + uu * 2048;
 #pragma unroll
-            for (int k = 0; k < 32; ++k) x[k] = pr.value(S.psi, a, lane | (k << 5));
+                for (int k = 0; k < 32; ++k) x[k] = pr.value_rows(rw, rw + 1024, a, lane | (k << 5));
+            } else {
+#pragma unroll
+                for (int k = 0; k < 32; ++k) x[k] = pr.value(S.psi, a, lane | (k << 5));
+            }
             reg_fwht<5, 0, 5>(x);
             tile_rounds<10, 0, 5, 1>(x, sm, lane, SyncWarp());
 #pragma unroll
@@ -88,8 +101,10 @@ __device__ __forceinline__ bool g3_pass1(const G3State& S, const G3Ctl& C, int64
     return true;
 }
 
-// ---- pass 2: tile r of batch g; adds 16 sum(R^4+I^4) and 4 sum(R^2+I^2) into acc/acc1 (thread 0)
-// If s2_atomic is given, thread 0 also adds this task's two sums to it before the task's release.
+// ---- pass 2: tile r of batch g; adds 16 sum(R^4+I^4) and 4 sum(R^2+I^2) of each warp's values
+// into acc/acc1 of that warp's lane 0 (no CTA barrier for the sums; the caller combines the 8
+// warps at the end).  If s2_atomic is given, lane 0 of every warp also adds its two sums to it
+// before the task's release.
 // FWD: forward only (M_2 without the gradient): no cube, back-transform or store.
 template <int M, bool FWD = false>
 __device__ __forceinline__ bool g3_pass2(const G3State& S, const G3Ctl& C, int64_t g, int r, float2* smem,
@@ -98,8 +113,7 @@ __device__ __forceinline__ bool g3_pass2(const G3State& S, const G3Ctl& C, int64
     constexpr int B0 = LOGT > 8 ? LOGT - 8 : 0;  // round-0 register bits that are columns
     using S2 = TileSched<13, LOGT, 5>;
     constexpr int SL2 = S2::last_shift();
-    __shared__ float red[8][2];
-    const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const uint32_t tid = threadIdx.x, lane = tid & 31;
     const int slot = (int)(g % S.R);
     if (!cta_wait_geq(S.done1 + slot, (unsigned)((g / S.R + 1) * S.p1) + C.wait_bias, C.status, C.spin_limit))
         return false;
@@ -142,11 +156,8 @@ __device__ __forceinline__ bool g3_pass2(const G3State& S, const G3Ctl& C, int64
         }
 #pragma unroll
         for (int o = 16; o >= 1; o >>= 1) { q += __shfl_xor_sync(0xffffffffu, q, o); s1 += __shfl_xor_sync(0xffffffffu, s1, o); }
-        if (lane == 0) { red[warp][0] = q; red[warp][1] = s1; }
-        __syncthreads();
-        if (tid == 0) {
-            double t0 = 0.0, t1 = 0.0;
-            for (int w = 0; w < 8; ++w) { t0 += 16.0 * (double)red[w][0]; t1 += 4.0 * (double)red[w][1]; }
+        if (lane == 0) {
+            const double t0 = 16.0 * (double)q, t1 = 4.0 * (double)s1;
             acc += t0;
             acc1 += t1;
             if (s2_atomic) { atomicAdd(s2_atomic, t0); atomicAdd(s2_atomic + 1, t1); }

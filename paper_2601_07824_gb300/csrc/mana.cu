@@ -15,6 +15,13 @@
 //   * 9 <= N <= 13: persistent two-pass kernel (same task order and bounded waits as the
 //     qubit kernel): pass 1 transforms the 8 low digits of one (a, unit) in a 3^8 tile, pass 2
 //     the N-8 high digits of 3^(N-8) units x 3^(16-N) columns and reduces.
+//     Since every chi_a is real and F_3^{(x)N} is linear, one complex transform of
+//     v_a + i v_a2 gives chi_a (real part) and chi_a2 (imaginary part).  The two-pass kernels
+//     transform such pairs: a2 = a + 3^j differs from a in one digit j >= 8, which in pass 1 is
+//     a digit of the unit, so the gather indices of a2 are those of a plus one offset per task.
+//     Level k (0 <= k < N - 8) pairs the X-strings with digits above j = N - 1 - k equal to 2
+//     and digit j equal to 0 with their digit-j-equal-1 partners; the 3^8 X-strings whose top
+//     N - 8 digits are all 2 are transformed alone.  About half the transforms remain.
 //
 // Mixed states (Sec. 3.3.3, Algorithm 6) run the same kernels with MIXED = true: with
 // rho = |psi><psi| the value above is rho[-x-a, x-a], and for a general density matrix
@@ -45,16 +52,16 @@ __device__ __forceinline__ void bfly3(float2& x0, float2& x1, float2& x2) {
 }
 
 // Butterflies over register digits [D0, D1) of an array of 3^E values (digit j has stride 3^j).
+// One digit per template level, so that every index into x is a compile-time constant and x
+// stays in registers.
 template <int E, int D0, int D1>
 __device__ __forceinline__ void reg_ft3(float2 (&x)[pow3(E)]) {
-#pragma unroll
-    for (int dgt = D0; dgt < D1; ++dgt) {
-        constexpr int dummy = 0;
-        (void)dummy;
-        const int st = pow3(dgt);
+    if constexpr (D0 < D1) {
+        constexpr int st = pow3(D0);
 #pragma unroll
         for (int r = 0; r < pow3(E); ++r)
             if ((r / st) % 3 == 0) bfly3(x[r], x[r + st], x[r + 2 * st]);
+        reg_ft3<E, D0 + 1, D1>(x);
     }
 }
 
@@ -152,14 +159,54 @@ __device__ __forceinline__ void load_pairs(float2 (&x)[pow3(E)], const PairIdx3&
     }
 }
 
-// Accumulate [sum |Re chi|, sum Re chi, sum (Re chi)^2] over a thread's values.
-template <int E>
+// v_a + i v_a2 where the gather indices of a2 are those of a plus `off` (both of them).
+template <int E, bool MIXED, int R = 0>
+__device__ __forceinline__ void load_pairs2(float2 (&x)[pow3(E)], const PairIdx3& pi, const float2* __restrict__ src,
+                                            int64_t dim, int64_t off) {
+    if constexpr (R < pow3(E)) {
+        const float2 v = pi.value<R, MIXED>(src, dim);
+        PairIdx3 q2 = pi;
+        q2.b1 += off;
+        q2.b2 += off;
+        const float2 w = q2.value<R, MIXED>(src, dim);
+        x[R] = make_float2(v.x - w.y, v.y + w.x);
+        load_pairs2<E, MIXED, R + 1>(x, pi, src, dim, off);
+    }
+}
+
+// Work item w of the two-pass kernels (see the file comment): X-string a and its partner
+// a2 = a + 3^j (a2 = -1 for a single).
+__device__ __forceinline__ void pair_item(int64_t w, int N, int64_t& a, int64_t& a2, int& j) {
+    int64_t base = 0, sz = pow3(N - 1);
+    for (int k = 0; k < N - 8; ++k, sz /= 3) {
+        if (w < sz) {
+            a = base + w;
+            a2 = a + sz;
+            j = N - 1 - k;
+            return;
+        }
+        w -= sz;
+        base += 2 * sz;  // digit N - 1 - k is 2 from here on
+    }
+    a = base + w;
+    a2 = -1;
+    j = -1;
+}
+
+// Accumulate [sum |chi|, sum chi, sum chi^2] over a thread's values; PAIRED: both parts of
+// each value are chi values (of two X-strings), else only the real part.
+template <int E, bool PAIRED = false>
 __device__ __forceinline__ void acc_chi(const float2 (&x)[pow3(E)], float& m, float& s, float& q) {
 #pragma unroll
     for (int r = 0; r < pow3(E); ++r) {
         m += fabsf(x[r].x);
         s += x[r].x;
         q = fmaf(x[r].x, x[r].x, q);
+        if constexpr (PAIRED) {
+            m += fabsf(x[r].y);
+            s += x[r].y;
+            q = fmaf(x[r].y, x[r].y, q);
+        }
     }
 }
 
@@ -258,15 +305,27 @@ __global__ void __launch_bounds__(256, 2) mana_twopass(ManaParams P) {
         if (kind == 1) {
             if (g >= P.R && !cta_wait_geq(P.done2 + slot, (unsigned)((g / P.R) * P.p2) + P.wait_bias, P.status, P.spin_limit))
                 return;
-            // one (a, unit) per task: tile x = unit * 3^8 + l, registers = digits [5, 8) of l
+            // one (work item, unit) per task: tile x = unit * 3^8 + l, registers = digits [5, 8) of l
             const int a_idx = r / pow3(M), unit = r % pow3(M);
-            const int64_t a = g * P.A + a_idx;
-            if (a < P.count) {
+            const int64_t w = g * P.A + a_idx;
+            if (w < P.count) {
                 float2 x[27];
                 using S = Sched3<D, 0, 3>;
+                int64_t a, a2;
+                int jd;
+                pair_item(w, N, a, a2, jd);
                 PairIdx3 pi;
                 pi.init<3>((int64_t)unit * TILE + deposit3<3>(t, 0, S::S0), a, N, S::S0);
-                load_pairs<3, MIXED>(x, pi, P.psi, PER_A);
+                if (a2 >= 0) {
+                    // digit jd of a is 0 and of a2 is 1; with x's digit xd (a digit of the unit),
+                    // both gather indices move by (xd == 0 ? +2 : -1) 3^jd
+                    int64_t pj = 1;
+                    for (int q = 8; q < jd; ++q) pj *= 3;
+                    const int xd = (int)((unit / pj) % 3);
+                    load_pairs2<3, MIXED>(x, pi, P.psi, PER_A, (xd == 0 ? 2 : -1) * pj * TILE);
+                } else {
+                    load_pairs<3, MIXED>(x, pi, P.psi, PER_A);
+                }
                 reg_ft3<3, 0, 3>(x);
                 rounds3<D, 0, 3, 1>(x, smem, t, act, SyncCta());
                 if (act) {
@@ -285,8 +344,8 @@ __global__ void __launch_bounds__(256, 2) mana_twopass(ManaParams P) {
             if (!cta_wait_geq(P.done1 + slot, (unsigned)((g / P.R + 1) * P.p1) + P.wait_bias, P.status, P.spin_limit))
                 return;
             const int a_idx = r / TILES, tile = r % TILES;
-            const int64_t a = g * P.A + a_idx;
-            if (a < P.count) {
+            const int64_t w = g * P.A + a_idx;
+            if (w < P.count) {
                 const float2* src = sbase + a_idx * PER_A + (int64_t)tile * T;
                 float2 x[27];
                 using S = Sched3<D, LOGT3, 3>;
@@ -298,7 +357,7 @@ __global__ void __launch_bounds__(256, 2) mana_twopass(ManaParams P) {
                 reg_ft3<3, (LOGT3 > S::S0 ? LOGT3 - S::S0 : 0), 3>(x);
                 rounds3<D, LOGT3, 3, 1>(x, smem, t, act, SyncCta());
                 float m = 0.f, s = 0.f, q = 0.f;
-                if (act) acc_chi<3>(x, m, s, q);
+                if (act) acc_chi<3, true>(x, m, s, q);  // a single's imaginary parts are zero
                 double v[3];
                 cta_sum3(m, s, q, v);
                 if (tid == 0) { acc[0] += v[0]; acc[1] += v[1]; acc[2] += v[2]; }
@@ -346,6 +405,12 @@ static cudaError_t twopass_prep(int* occ) {
 }  // namespace mana
 
 int mana_tiles_per_a(int N) { return N <= 8 ? 1 : mana::pow3(8) / mana::pow3(16 - N); }
+
+int64_t mana_pair_items(int N) {
+    int64_t n = mana::pow3(8);
+    for (int k = 0; k < N - 8; ++k) n += mana::pow3(N - 1 - k);
+    return n;
+}
 
 cudaError_t launch_mana_onepass(const float2* src, int N, bool mixed, double* out, int sm_count, int* grid,
                                 cudaStream_t st) {

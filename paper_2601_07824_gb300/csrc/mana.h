@@ -8,8 +8,8 @@ namespace hm {
 struct ManaParams {
     const float2* psi;       // the state, or the density matrix for mixed states
     int N;
-    int64_t count;           // number of X-strings a (3^N)
-    float2* scratch;         // R slots x A X-strings x 3^N values
+    int64_t count;           // number of work items (mana_pair_items(N)): X-string pairs and singles
+    float2* scratch;         // R slots x A work items x 3^N values
     int R, A;
     int64_t n_batches;
     int p1, p2;              // tasks per batch (A * 3^(N-8) each)
@@ -22,6 +22,8 @@ struct ManaParams {
 };
 
 int mana_tiles_per_a(int N);
+// Work items of the two-pass kernels (9 <= N <= 13): sum_{k < N-8} 3^(N-1-k) pairs + 3^8 singles.
+int64_t mana_pair_items(int N);
 // mixed = false: src is the N-qutrit state psi (3^N values, Algorithm 5); mixed = true: src is
 // a density matrix rho, 3^N x 3^N row-major (Algorithm 6's W via the same transform; the
 // two-pass variant exists for N = 9, 10).

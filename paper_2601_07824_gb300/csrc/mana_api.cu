@@ -40,8 +40,8 @@ hadamag_status mana_sums(hadamag_ctx_t c, const void* psi, int N, hadamag_dtype 
         int A = 8;
         while (A > 1 && (size_t)A * per_a > ((size_t)16 << 20)) A >>= 1;
         ManaParams P{};
-        P.psi = p; P.N = N; P.count = dim; P.R = 3; P.A = A;
-        P.n_batches = (dim + A - 1) / A;
+        P.psi = p; P.N = N; P.count = mana_pair_items(N); P.R = 3; P.A = A;
+        P.n_batches = (P.count + A - 1) / A;
         P.p1 = P.p2 = A * (int)ipow3(M);
         int grid = 0;
         if ((e = mana_twopass_grid(N, mixed, c->sm_count, &grid)) != cudaSuccess) return cuda_fail(c, e, "occupancy");

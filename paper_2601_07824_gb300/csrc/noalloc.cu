@@ -102,9 +102,12 @@ extern "C" hadamag_status hadamag_sre_noalloc(const void* psi_dev, int N, double
     P.R = 2;  // two slots: the smallest ring the task order allows
     P.A = 1;
     P.U = 8;
+    P.UPW = 2;
+    P.TPT = 2;
+    P.a_base = 0;
     P.n_batches = P.count;
-    P.p1 = (1 << M) / (P.U * 2);
-    P.p2 = twopass_tiles_per_a(N) / 2;
+    P.p1 = (1 << M) / (P.U * P.UPW);
+    P.p2 = twopass_tiles_per_a(N) / P.TPT;
     P.done1 = reinterpret_cast<unsigned*>(base + kCounterOff);
     P.done2 = P.done1 + 64;
     P.status = reinterpret_cast<int*>(base + kStatusOff);

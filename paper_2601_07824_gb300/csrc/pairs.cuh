@@ -66,6 +66,35 @@ struct PairRows {
 };
 
 
+// Shared-memory slots of a pass-1 row staging (2 units x own/partner row of 2^10 values).
+constexpr uint32_t kStageSlots = 4u << 10;
+
+// Copies the four state rows that the pair products of X-string a on units unit and unit + 1
+// read (PairRows' row A and row B of each unit, 2^10 values each) into rows[0 .. 4 x 2^10):
+// unit uu's rows at rows + 2048 uu (row A) and + 1024 (row B).  cp.async by the 256 threads of
+// the CTA; every thread returns once the copy has landed (one CTA barrier).
+template <int M>
+__device__ __forceinline__ void stage_rows(float2* rows, const float2* __restrict__ psi, int64_t a, int64_t unit) {
+    int64_t rb[4];
+#pragma unroll
+    for (int uu = 0; uu < 2; ++uu) {
+        const PairRows<10, M> pr(a, unit + uu);
+        rb[2 * uu] = pr.rowA;
+        rb[2 * uu + 1] = pr.rowB;
+    }
+    // 2048 16-byte chunks, 8 per thread: chunk tid + 256 q is in row q / 2 at value offset
+    // 2 (tid + 256 (q % 2))
+    const uint32_t tid = threadIdx.x;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+        const uint32_t off = (tid + 256u * (q & 1)) * 2u;
+        cp_async16(rows + (q >> 1) * 1024u + off, psi + rb[q >> 1] + off);
+    }
+    cp_async_commit();
+    cp_async_wait<0>();
+    __syncthreads();
+}
+
 // Pair product of the half-length form for z' (no unit split; used by the one-pass kernels).
 __device__ __forceinline__ float2 pair_product(const float2* __restrict__ psi, int64_t zp, int64_t a, int p) {
     if (a != 0) {

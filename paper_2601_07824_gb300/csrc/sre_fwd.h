@@ -19,7 +19,8 @@ struct OnepassArgs {
     int N;
     double nq;               // Renyi index n
     int64_t count;           // number of X-strings (2^N, or the list length)
-    const int64_t* a_list;   // nullptr: a = 0 .. count-1
+    const int64_t* a_list;   // nullptr: a = a_base .. a_base + count-1
+    int64_t a_base;
     double* out;             // per_a: [count][3]; else per-CTA [grid][3]
     int per_a;
     int* status;
@@ -33,9 +34,11 @@ struct TwoPassParams {
     int64_t count;
     const int64_t* a_list;
     float2* scratch;         // R slots x A X-strings x 2^(N-1) complex values
-    int R, A, U;             // slots, X-strings per batch, units per pass-1 task (A*U = 8 or 1)
+    int R, A, U;             // slots, X-strings per batch, warps per X-string in pass 1 (A*U = 8 or 1)
+    int UPW, TPT;            // units per pass-1 warp (K1 = 10; even), column tiles per pass-2 task
     int64_t n_batches;
     int p1, p2;              // pass-1 / pass-2 tasks per batch
+    int64_t a_base;          // without a list: X-string of entry i is a_base + i
     unsigned* done1;         // per slot: finished pass-1 tasks (monotonic)
     unsigned* done2;         // per slot: finished pass-2 tasks (monotonic)
     int* status;
@@ -66,7 +69,7 @@ struct HbmParams {
 int hbm_tiles_per_a(int N);
 cudaError_t launch_hbm(const HbmParams& P, int sm_count, int* grid, cudaStream_t st);
 
-// Two-pass geometry for N in [16, 24]: pass 1 transforms K1 = twopass_k1(N) bits (10 or 13),
+// Two-pass geometry for N in [15, 24]: pass 1 transforms K1 = twopass_k1(N) bits (10 or 13),
 // pass 2 the other N-1-K1 bits, in tiles of 2^13 values; tiles per X-string:
 int twopass_tiles_per_a(int N);
 // per-X-string output triples of the two-pass kernel (one per tile and warp)

@@ -34,7 +34,7 @@ namespace hm {
 template <int L, int MODE>
 __global__ void __launch_bounds__(OnepassShape<L>::NT)
 sre_onepass(const float2* __restrict__ psi, int N, double nq, int64_t count,
-            const int64_t* __restrict__ a_list, double* __restrict__ out, int per_a, int* status) {
+            const int64_t* __restrict__ a_list, int64_t a_base, double* __restrict__ out, int per_a, int* status) {
     using Sh = OnepassShape<L>;
     constexpr int E = Sh::E, G = Sh::G, GPC = Sh::GPC;
     using S = TileSched<L, 0, E>;
@@ -52,7 +52,7 @@ sre_onepass(const float2* __restrict__ psi, int N, double nq, int64_t count,
     for (int64_t it = 0; it < iters; ++it) {
         const int64_t idx = gg + it * ngroups;
         bool valid = idx < count;
-        int64_t a = valid ? (a_list ? a_list[idx] : idx) : 0;
+        int64_t a = valid ? (a_list ? a_list[idx] : a_base + idx) : 0;
         if (a < 0 || a >= dim) {
             if (valid) atomicOr(status, ST_BADARG);
             valid = false;
@@ -112,9 +112,6 @@ sre_onepass(const float2* __restrict__ psi, int N, double nq, int64_t count,
         }
     }
 }
-
-// Shared-memory slots of the pass-1 row staging (2 units x own/partner row of 2^10 values).
-constexpr uint32_t kStageSlots = 4u << 10;
 
 // ------------------------------------------------------------------------------------------
 // Persistent two-pass kernel, 256 threads per CTA (two CTAs per SM).
@@ -193,57 +190,43 @@ __global__ void __launch_bounds__(256, 2) sre_twopass(TwoPassParams P) {
             // ---- pass 1: pair product + transform over the K1 low bits of z' ----------------
             int a_idx, sub;
             int64_t unit;
-            if constexpr (K1 == 10) { a_idx = warp % P.A; unit = ((int64_t)r * P.U + warp / P.A) * 2; sub = warp; }
+            if constexpr (K1 == 10) { a_idx = warp % P.A; unit = ((int64_t)r * P.U + warp / P.A) * P.UPW; sub = warp; }
             else { a_idx = 0; unit = r; sub = 0; }
             const int64_t i = g * P.A + a_idx;
             bool valid = i < P.count;
-            int64_t a = valid ? (P.a_list ? P.a_list[i] : i) : 0;
+            int64_t a = valid ? (P.a_list ? P.a_list[i] : P.a_base + i) : 0;
             if (a < 0 || a >= dim) {
                 if (valid && (tid & (K1 == 10 ? 31 : 255)) == 0) atomicOr(P.status, ST_BADARG);
                 valid = false;
             }
-            bool stage = false;  // CTA-uniform
             if constexpr (K1 == 10) {
+                bool stage = false;  // CTA-uniform
+                int64_t a0 = 0;
                 if (P.U == 1) {
-                    // every warp on units (unit, unit + 1): rows shared when all X-strings of the
-                    // batch agree in their bits above K1 (always so without a list)
+                    // every warp on the same units: rows shared when all X-strings of the batch
+                    // agree in their bits above K1 (always so without a list)
                     const int64_t i0 = g * P.A;  // < count for every batch
-                    const int64_t a0 = P.a_list ? P.a_list[i0] : i0;
+                    a0 = P.a_list ? P.a_list[i0] : P.a_base + i0;
                     stage = a0 >= 0 && a0 < dim;
                     if (P.a_list) stage = __syncthreads_and(stage && (!valid || (a >> K1) == (a0 >> K1))) != 0;
-                    if (stage) {
-                        float2* rows = smem + 8 * tile_slots(10);
-                        int64_t rb[4];
-#pragma unroll
-                        for (int uu = 0; uu < 2; ++uu) {
-                            const PairRows<K1, M> pr0(a0, unit + uu);
-                            rb[2 * uu] = pr0.rowA;
-                            rb[2 * uu + 1] = pr0.rowB;
-                        }
-                        // 4 rows x 2^10 values = 2048 16-byte chunks, 8 per thread: chunk
-                        // tid + 256 q is in row q / 2 at value offset 2 (tid + 256 (q % 2))
-#pragma unroll
-                        for (int q = 0; q < 8; ++q) {
-                            const uint32_t off = (tid + 256u * (q & 1)) * 2u;
-                            cp_async16(rows + (q >> 1) * 1024u + off, psi + rb[q >> 1] + off);
-                        }
-                        cp_async_commit();
-                        cp_async_wait<0>();
-                        __syncthreads();
-                    }
                 }
-            }
-            if (valid) {
-                float2 x[32];
-                if constexpr (K1 == 10) {
-                    float2* sm = smem + sub * tile_slots(10);
-                    for (int uu = 0; uu < 2; ++uu) {  // two consecutive units per warp
-                        const PairRows<K1, M> pr(a, unit + uu);
-                        float2* dst = sbase + (size_t)a_idx * ((size_t)1 << L) + ((size_t)(unit + uu) << K1);
+                float2* sm = smem + sub * tile_slots(10);
+                float2* rows = smem + 8 * tile_slots(10);
+                for (int up = 0; up < P.UPW; up += 2) {  // UPW consecutive units per warp, two at a time
+                    if (stage) {
+                        if (up > 0) __syncthreads();  // every warp is done with the previous rows
+                        stage_rows<M>(rows, psi, a0, unit + up);
+                    }
+                    if (!valid) continue;
+                    float2 x[32];
+                    for (int uu = 0; uu < 2; ++uu) {
+                        const int64_t un = unit + up + uu;
+                        const PairRows<K1, M> pr(a, un);
+                        float2* dst = sbase + (size_t)a_idx * ((size_t)1 << L) + ((size_t)un << K1);
                         if (stage) {
-                            const float2* rows = smem + 8 * tile_slots(10) + uu * 2048;
+                            const float2* rw = rows + uu * 2048;
 #pragma unroll
-                            for (int k = 0; k < 32; ++k) x[k] = pr.value_rows(rows, rows + 1024, a, lane | (k << 5));
+                            for (int k = 0; k < 32; ++k) x[k] = pr.value_rows(rw, rw + 1024, a, lane | (k << 5));
                         } else {
 #pragma unroll
                             for (int k = 0; k < 32; ++k) x[k] = pr.value(psi, a, lane | (k << 5));
@@ -254,7 +237,10 @@ __global__ void __launch_bounds__(256, 2) sre_twopass(TwoPassParams P) {
 #pragma unroll
                         for (int k = 0; k < 32; ++k) __stcg(dst + lane + (k << 5), x[k]);
                     }
-                } else {
+                }
+            } else if (valid) {
+                float2 x[32];
+                {
                     const PairRows<K1, M> pr(a, unit);
                     float2* dst = sbase + (size_t)a_idx * ((size_t)1 << L) + ((size_t)unit << K1);
 #pragma unroll
@@ -273,9 +259,9 @@ __global__ void __launch_bounds__(256, 2) sre_twopass(TwoPassParams P) {
             }
         } else {
             // ---- pass 2: transform over the M high bits of z' + reduction ------------------
-            const int a_idx = r / (TILES / 2);
+            const int a_idx = r / (TILES / P.TPT);
             const int64_t i = g * P.A + a_idx;
-            if (i < P.count) for (int tile = (r % (TILES / 2)) * 2, te = tile + 2; tile < te; ++tile) {
+            if (i < P.count) for (int tile = (r % (TILES / P.TPT)) * P.TPT, te = tile + P.TPT; tile < te; ++tile) {
                 const float2* src = sbase + (size_t)a_idx * ((size_t)1 << L) + (size_t)tile * T;
                 float2 x[32];
 #pragma unroll
@@ -283,7 +269,9 @@ __global__ void __launch_bounds__(256, 2) sre_twopass(TwoPassParams P) {
                     const uint32_t j = deposit<5>(tid, k, 8);  // tile index (row << LOGT) | col
                     x[k] = __ldcg(src + ((size_t)(j >> LOGT) << K1) + (j & (T - 1)));
                 }
-                reg_fwht<5, 0, 5>(x);
+                // register bits are tile bits [8, 13); those below LOGT are column bits (N = 15)
+                constexpr int B0 = LOGT > 8 ? LOGT - 8 : 0;
+                reg_fwht<5, B0, 5>(x);
                 tile_rounds<13, LOGT, 5, 1>(x, smem, tid, SyncCta());
                 if constexpr (Sh::DISCARD) {
                     // every value of the tile is in registers: drop its lines from L2 unwritten
@@ -350,7 +338,7 @@ static cudaError_t launch_onepass_t(OnepassArgs& A, int sm_count, cudaStream_t s
     if (A.grid > 0 && A.grid < cap) cap = A.grid;
     A.grid = (int)(need < cap ? need : cap);
     if (A.grid < 1) A.grid = 1;
-    k<<<A.grid, Sh::NT, smem, st>>>(A.psi, A.N, A.nq, A.count, A.a_list, A.out, A.per_a, A.status);
+    k<<<A.grid, Sh::NT, smem, st>>>(A.psi, A.N, A.nq, A.count, A.a_list, A.a_base, A.out, A.per_a, A.status);
     return cudaGetLastError();
 }
 
@@ -392,9 +380,11 @@ static cudaError_t launch_twopass_t(const TwoPassParams& P, int grid, cudaStream
     return cudaGetLastError();
 }
 
-// N -> (K1, M): N = 16..20 -> (10, N-11); N = 21..24 -> (13, N-14).
+// N -> (K1, M): N = 15..20 -> (10, N-11); N = 21..24 -> (13, N-14).  (N = 15 runs two passes
+// only when the autotuner picks them over the one-pass kernel.)
 #define HM_TWOPASS_SWITCH(N_, EXPR)                                              \
     switch (N_) {                                                                \
+        case 15: { constexpr int KK = 10, MM = 4; EXPR; }                        \
         case 16: { constexpr int KK = 10, MM = 5; EXPR; }                        \
         case 17: { constexpr int KK = 10, MM = 6; EXPR; }                        \
         case 18: { constexpr int KK = 10, MM = 7; EXPR; }                        \

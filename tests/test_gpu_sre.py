@@ -4,6 +4,8 @@ Tolerance (stated for the FP32 path): |dM| <= 1e-6 * max(1, |M|), i.e. 1e-6 rela
 |M| >= 1 and 1e-6 absolute near stabilizer states where M = 0; per-X-string sums agree to
 2e-5 relative (FP32 transform of 2^(N-1) values, FP32 partial sums).  Index work (the
 SplitMix64 X-strings) is compared bit for bit."""
+import ctypes
+
 import numpy as np
 import pytest
 
@@ -183,5 +185,61 @@ def test_wait_timeout_is_reported_and_recoverable():
                                ctypes.c_void_p(torch.cuda.current_stream().cuda_stream))
         assert rc == 0
         assert close_M(M.value, hm.sre(t, 2.0)[0], 1e-12)
+    finally:
+        c.close()
+
+
+@pytest.mark.parametrize("N", [16, 18, 20])
+def test_autotuned_shape_matches_default_shape(N):
+    # the two-pass autotuner picks task shapes per (N, n); every shape computes the same sums
+    # (up to the order of the FP64 partials), and a tuned context reports its choice
+    from paper_2601_07824_gb300._lib import Context
+    psi = torch.from_numpy(I.brickwork_haar(N, 6, seed=880 + N, dtype=np.complex64)).to(DEV)
+    tuned, plain = Context(0), Context(0)
+    try:
+        plain.set_autotune(False)
+        out = {}
+        for c in (tuned, plain):
+            M, ln = ctypes.c_double(), ctypes.c_double()
+            c.check(c.lib.hadamag_sre(c.h, ctypes.c_void_p(psi.data_ptr()), N, 2.0, 0, ctypes.byref(M),
+                                      ctypes.byref(ln), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)),
+                    "hadamag_sre")
+            out[id(c)] = M.value
+        shape = tuned.twopass_shape(N, 2.0)
+        assert shape[0] in (2, 4) and shape[1] in (2, 4) and shape[2] in (3, 4) and shape[3] == 8, shape
+        assert plain.twopass_shape(N, 2.0) == [0, 0, 0, 0]
+        assert abs(out[id(tuned)] - out[id(plain)]) <= 1e-12 * abs(out[id(plain)])
+    finally:
+        tuned.close()
+        plain.close()
+
+
+def _sre_with(c, psi, N, n):
+    M, ln = ctypes.c_double(), ctypes.c_double()
+    c.check(c.lib.hadamag_sre(c.h, ctypes.c_void_p(psi.data_ptr()), N, float(n), 0, ctypes.byref(M),
+                              ctypes.byref(ln), ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)),
+            "hadamag_sre")
+    return M.value, ln.value
+
+
+@pytest.mark.parametrize("n", [2.0, 1.0, 3.0])
+def test_N15_one_pass_and_two_pass_splits_vs_oracle(n):
+    # N = 15 runs either the one-pass kernel (whole transform in one CTA's shared memory) or two
+    # passes through L2 (10 + 4 bits), whichever the tuner picks; both against the oracle
+    from paper_2601_07824_gb300._lib import Context
+    N = 15
+    psi_np = I.gaussian_state(N, 1515, dtype=np.complex64)
+    psi = torch.from_numpy(psi_np).to(DEV)
+    Mo, lno = oracle.sre(psi_np, n)
+    c = Context(0)
+    try:
+        for upw, tpt in ((-1, 0), (2, 1), (2, 2), (4, 1), (4, 2)):
+            c.set_twopass_shape(N, n, upw, tpt)
+            M, ln = _sre_with(c, psi, N, n)
+            assert abs(M - Mo) <= TOL_M * max(1.0, abs(Mo)), (upw, tpt, M, Mo)
+            assert abs(ln - lno) <= 1e-6
+            assert c.twopass_shape(N, n) == ([-1] * 4 if upw == -1 else [upw, tpt, 4, 8])
+        with pytest.raises(Exception):
+            c.set_twopass_shape(N, n, 3, 1)
     finally:
         c.close()

@@ -101,3 +101,21 @@ def test_mc_estimator_treats_identity_row_exactly():
     exact = f(psi)
     Shat_all = Sq[0] / 2 ** N + (2 ** N - 1) / 2 ** N * Sq[1:].mean()
     assert abs(-np.log2(Shat_all) - exact) < 1e-12
+
+
+def test_gradient_at_N17_matches_stored_finite_differences():
+    # tests/golden/grad_large.json (tests/golden/make_grad_fd_values.py, oracle only): at N = 17
+    # the oracle's gradient projected on seeded directions equals central finite differences of
+    # its forward M_2 (step 1e-4) -- the same pin as above at a size too slow to rerun here
+    import json
+    import os
+    with open(os.path.join(os.path.dirname(__file__), "golden", "grad_large.json")) as f:
+        gold = json.load(f)
+    checked = 0
+    for name, e in gold.items():
+        if name.startswith("_"):
+            continue
+        for k, fd in enumerate(e["fd"]):
+            assert abs(fd - e["proj"][k]) <= 1e-6 * abs(e["proj"][k]) + 1e-10, (name, k, fd, e["proj"][k])
+            checked += 1
+    assert checked >= 2
