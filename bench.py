@@ -418,7 +418,7 @@ def main():
                        "l2": f"state ({psi_np.nbytes >> 20} MiB) is smaller than L2: a 256 MiB buffer is written between steps",
                        "M2": M, "lost_norm": ln,
                        "twopass_shape": (dict(zip(("units_per_pass1_warp", "tiles_per_pass2_task", "ring_slots",
-                                                   "xstrings_per_batch"), ctx.twopass_shape(N, 2.0)))
+                                                   "xstrings_per_batch", "pass2_lag"), ctx.twopass_shape(N, 2.0)))
                                          if 16 <= N <= 24 else None)},
             "roofline": roof,
             "clocks": clocks,

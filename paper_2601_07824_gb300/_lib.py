@@ -89,7 +89,7 @@ def load(path: str | None = None):
             "hadamag_sre_chunk": [I],
             "hadamag_set_autotune": [V, I],
             "hadamag_twopass_shape": [V, I, D, ctypes.POINTER(I)],
-            "hadamag_set_twopass_shape": [V, I, D, I, I, I],
+            "hadamag_set_twopass_shape": [V, I, D, I, I, I, I],
             "hadamag_sre_slice": [V, V, I, D, I, L, L, V, V],
             "hadamag_sre_combine": [I, D, PD, L, PD, PD],
             "hadamag_sre_grad_slice": [V, V, I, I, L, L, PD, V, V],
@@ -154,16 +154,16 @@ class Context:
         self.check(self.lib.hadamag_set_autotune(self.h, 1 if on else 0), "hadamag_set_autotune")
 
     def twopass_shape(self, N: int, n: float = 2.0):
-        """[units per pass-1 warp, tiles per pass-2 task, ring slots, X-strings per batch] in use
-        for (N, n); zeros before the tuner ran."""
-        out = (ctypes.c_int * 4)()
+        """[units per pass-1 warp, tiles per pass-2 task, ring slots, X-strings per batch, lag] in
+        use for (N, n); zeros before the tuner ran."""
+        out = (ctypes.c_int * 5)()
         self.check(self.lib.hadamag_twopass_shape(self.h, int(N), float(n), out), "hadamag_twopass_shape")
         return list(out)
 
-    def set_twopass_shape(self, N: int, n: float, upw: int, tpt: int, R: int = 0):
+    def set_twopass_shape(self, N: int, n: float, upw: int, tpt: int, R: int = 0, lag: int = 1):
         """Pin the two-pass shape for (N, n) (see hadamag_set_twopass_shape)."""
-        self.check(self.lib.hadamag_set_twopass_shape(self.h, int(N), float(n), int(upw), int(tpt), int(R)),
-                   "hadamag_set_twopass_shape")
+        self.check(self.lib.hadamag_set_twopass_shape(self.h, int(N), float(n), int(upw), int(tpt), int(R),
+                                                      int(lag)), "hadamag_set_twopass_shape")
 
     def set_wait_limit(self, spins: int, bias: int = 0):
         self.check(self.lib.hadamag_set_wait_limit(self.h, int(spins), int(bias)), "hadamag_set_wait_limit")

@@ -87,8 +87,9 @@ hadamag_status as_c64(hadamag_ctx_t c, const void* psi, int64_t n, hadamag_dtype
 int sre_mode(double n) { return n == 1.0 ? 1 : n == 2.0 ? 2 : n == 3.0 ? 3 : 0; }
 
 // Two-pass launch shape for N: X-strings per batch A, ring slots R (0: the default), units per
-// pass-1 warp UPW (K1 = 10) and column tiles per pass-2 task TPT.
-TwoPlan plan_twopass(int N, int UPW, int TPT, int R) {
+// pass-1 warp UPW (K1 = 10), column tiles per pass-2 task TPT, and the lag (stages) between a
+// batch's pass 1 and its pass 2 (1 <= lag < R).
+TwoPlan plan_twopass(int N, int UPW, int TPT, int R, int lag) {
     TwoPlan p{};
     const int L = N - 1, K1 = twopass_k1(N), M = L - K1;
     const size_t per_a = ((size_t)1 << L) * sizeof(float2);
@@ -108,6 +109,7 @@ TwoPlan plan_twopass(int N, int UPW, int TPT, int R) {
     p.triples = twopass_triples_per_a(N);
     p.UPW = (K1 == 10) ? UPW : 1;
     p.TPT = TPT;
+    p.lag = lag < p.R ? lag : p.R - 1;
     // a pass-1 task covers A X-strings x (U or 1) warps x UPW units per warp (K1 = 10), or one
     // unit (K1 = 13); a pass-2 task covers TPT adjacent column tiles
     p.p1 = (K1 == 10) ? (1 << M) / (p.U * p.UPW) : (1 << M);
@@ -147,7 +149,7 @@ hadamag_status run_sre(hadamag_ctx_t c, const float2* psi, int N, double n, int6
     if (N > 24) return fail(c, HADAMAG_ERR_UNSUPPORTED, "exact SRE supports N <= 24 (got %d)", N);
     if ((s = tune_twopass(c, psi, N, n, mode, st))) return s;
     const TwoShape& sh = c->twopass_shape[N][mode];
-    TwoPlan pl = sh.UPW ? plan_twopass(N, sh.UPW, sh.TPT, sh.R) : plan_twopass(N);
+    TwoPlan pl = sh.UPW ? plan_twopass(N, sh.UPW, sh.TPT, sh.R, sh.lag) : plan_twopass(N);
     return launch_twopass_plan(c, psi, N, n, mode, pl, count, a_list, 0, per_a, terms, st, nparts);
 }
 
@@ -164,7 +166,7 @@ hadamag_status launch_twopass_plan(hadamag_ctx_t c, const float2* psi, int N, do
     TwoPassParams P{};
     P.psi = psi; P.N = N; P.nq = n; P.count = count; P.a_list = a_list; P.a_base = a_base;
     P.scratch = (float2*)c->scratch.ptr; P.R = pl.R; P.A = pl.A; P.U = pl.U;
-    P.UPW = pl.UPW; P.TPT = pl.TPT;
+    P.UPW = pl.UPW; P.TPT = pl.TPT; P.lag = pl.lag;
     P.n_batches = (count + pl.A - 1) / pl.A;
     P.p1 = pl.p1; P.p2 = pl.p2;
     P.done1 = (unsigned*)c->counters.ptr; P.done2 = P.done1 + 64;
@@ -197,8 +199,8 @@ hadamag_status launch_twopass_plan(hadamag_ctx_t c, const float2* psi, int N, do
 // The two-pass autotuner: on the first uncaptured call for (N, mode) it times each candidate
 // task shape on a bounded range of X-strings (a >= 2^(N-1), the common kind; two launches each,
 // the second timed with CUDA events on the call's stream) and keeps the fastest for the context.
-// Candidates: units per pass-1 warp {2, 4} (K1 = 10) x tiles per pass-2 task {2, 4}, and for
-// N = 20 also 3 or 4 ring slots.  At N = 15 the split itself is tuned: the one-pass kernel (the
+// Candidates: units per pass-1 warp {2, 4} (K1 = 10) x tiles per pass-2 task {2, 4} x a pass-2
+// lag of 1 or 2 stages, and for N = 20 also 3 or 4 ring slots.  At N = 15 the split itself is tuned: the one-pass kernel (the
 // whole 2^14-value transform in one CTA's shared memory) against two passes through L2 (10 + 4
 // bits; tiles per pass-2 task {1, 2}).  Under stream capture, or with autotuning off, the
 // defaults run (one pass at N = 15).
@@ -209,17 +211,23 @@ hadamag_status tune_twopass(hadamag_ctx_t c, const float2* psi, int N, double n,
     cudaError_t e;
     if ((e = cudaStreamIsCapturing(st, &cap)) != cudaSuccess) return cuda_fail(c, e, "capture query");
     if (cap != cudaStreamCaptureStatusNone) return HADAMAG_OK;
-    struct Cand { int UPW, TPT, R; };  // UPW 0: the one-pass kernel (N = 15)
-    Cand cands[16];
+    struct Cand { int UPW, TPT, R, lag; };  // UPW 0: the one-pass kernel (N = 15)
+    Cand cands[32];
     int nc = 0;
     const bool k10 = twopass_k1(N) == 10;
-    if (N == 15) cands[nc++] = {0, 0, 0};
+    if (N == 15) cands[nc++] = {0, 0, 0, 1};
     for (int upw : {2, 4}) {
         if (!k10 && upw != 2) continue;
         for (int tpt : {1, 2, 4}) {
             if (tpt > twopass_tiles_per_a(N) || (tpt == 1 && N != 15)) continue;
-            if (N == 20) { cands[nc++] = {upw, tpt, 3}; cands[nc++] = {upw, tpt, 4}; }
-            else cands[nc++] = {upw, tpt, 0};
+            for (int lag : {1, 2}) {
+                if (N == 20) {
+                    cands[nc++] = {upw, tpt, 3, lag};
+                    if (lag == 1) cands[nc++] = {upw, tpt, 4, lag};
+                } else {
+                    cands[nc++] = {upw, tpt, 0, lag};
+                }
+            }
         }
     }
     const int64_t cnt = int64_t(1) << (N <= 20 ? 13 : 10);
@@ -231,7 +239,8 @@ hadamag_status tune_twopass(hadamag_ctx_t c, const float2* psi, int N, double n,
     Cand win = cands[0];
     hadamag_status s = HADAMAG_OK;
     for (int k = 0; k < nc && !s; ++k) {
-        const TwoPlan pl = cands[k].UPW ? plan_twopass(N, cands[k].UPW, cands[k].TPT, cands[k].R) : TwoPlan{};
+        const TwoPlan pl = cands[k].UPW ? plan_twopass(N, cands[k].UPW, cands[k].TPT, cands[k].R, cands[k].lag)
+                                        : TwoPlan{};
         for (int rep = 0; rep < 2 && !s; ++rep) {
             if (rep == 1) cudaEventRecord(e0, st);
             int64_t np = 0;
@@ -263,6 +272,7 @@ hadamag_status tune_twopass(hadamag_ctx_t c, const float2* psi, int N, double n,
     sh.UPW = win.UPW;
     sh.TPT = win.TPT;
     sh.R = win.R;
+    sh.lag = win.lag;
     sh.onepass = win.UPW == 0;
     return HADAMAG_OK;
 }
@@ -377,24 +387,26 @@ extern "C" hadamag_status hadamag_set_autotune(hadamag_ctx_t c, int on) {
     return HADAMAG_OK;
 }
 
-extern "C" hadamag_status hadamag_twopass_shape(hadamag_ctx_t c, int N, double n, int* out4) {
-    if (!c || !out4 || N < 15 || N > 24 || !(n > 0.0)) return HADAMAG_ERR_INVALID_ARG;
+extern "C" hadamag_status hadamag_twopass_shape(hadamag_ctx_t c, int N, double n, int* out5) {
+    if (!c || !out5 || N < 15 || N > 24 || !(n > 0.0)) return HADAMAG_ERR_INVALID_ARG;
     int mode = sre_mode(n);
     if (mode == 0 && c->fp32_powers && n <= 4.0 && n * (N + 2) <= 100.0) mode = 4;
     const TwoShape& sh = c->twopass_shape[N][mode];
     if (sh.onepass) {
-        out4[0] = out4[1] = out4[2] = out4[3] = -1;
+        for (int k = 0; k < 5; ++k) out5[k] = -1;
         return HADAMAG_OK;
     }
-    const TwoPlan pl = sh.UPW ? plan_twopass(N, sh.UPW, sh.TPT, sh.R) : plan_twopass(N);
-    out4[0] = sh.UPW ? pl.UPW : 0;
-    out4[1] = sh.UPW ? pl.TPT : 0;
-    out4[2] = sh.UPW ? pl.R : 0;
-    out4[3] = sh.UPW ? pl.A : 0;
+    const TwoPlan pl = sh.UPW ? plan_twopass(N, sh.UPW, sh.TPT, sh.R, sh.lag) : plan_twopass(N);
+    out5[0] = sh.UPW ? pl.UPW : 0;
+    out5[1] = sh.UPW ? pl.TPT : 0;
+    out5[2] = sh.UPW ? pl.R : 0;
+    out5[3] = sh.UPW ? pl.A : 0;
+    out5[4] = sh.UPW ? pl.lag : 0;
     return HADAMAG_OK;
 }
 
-extern "C" hadamag_status hadamag_set_twopass_shape(hadamag_ctx_t c, int N, double n, int upw, int tpt, int R) {
+extern "C" hadamag_status hadamag_set_twopass_shape(hadamag_ctx_t c, int N, double n, int upw, int tpt, int R,
+                                                    int lag) {
     if (!c || N < 15 || N > 24 || !(n > 0.0)) return HADAMAG_ERR_INVALID_ARG;
     int mode = sre_mode(n);
     if (mode == 0 && c->fp32_powers && n <= 4.0 && n * (N + 2) <= 100.0) mode = 4;
@@ -406,11 +418,13 @@ extern "C" hadamag_status hadamag_set_twopass_shape(hadamag_ctx_t c, int N, doub
     }
     const bool k10 = twopass_k1(N) == 10;
     if ((k10 ? (upw != 2 && upw != 4) : upw != 2) || tpt < 1 || tpt > twopass_tiles_per_a(N) ||
-        (twopass_tiles_per_a(N) % tpt) || !(R == 0 || (R >= 2 && R <= 4)))
+        (twopass_tiles_per_a(N) % tpt) || !(R == 0 || (R >= 2 && R <= 4)) || lag < 1 ||
+        lag >= plan_twopass(N, upw, tpt, R).R)
         return HADAMAG_ERR_INVALID_ARG;
     sh.UPW = upw;
     sh.TPT = tpt;
     sh.R = R;
+    sh.lag = lag;
     sh.onepass = 0;
     return HADAMAG_OK;
 }

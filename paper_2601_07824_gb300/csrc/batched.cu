@@ -56,7 +56,7 @@ __device__ __forceinline__ bool large_task_fwd(const BatchState& s, const G3Ctl&
     // forward only: stage st = pass 1 of batch st, pass 2 of batch st - 1; a slot is reused once
     // its pass 2 is done (the done3 / p3 fields of the state view point at done2 / p2)
     const G3State S{s.psi, s.N, s.scratch, s.R, s.A, s.U, s.n_batches, s.p1, s.p2, s.p2,
-                    s.ctr, s.ctr + 64, s.ctr + 64};
+                    s.ctr, s.ctr + 64, s.ctr + 64, 0, s.UPW, s.TPT};
     const int64_t per_stage = (int64_t)s.p1 + s.p2;
     const int64_t st = local / per_stage;
     int r = (int)(local % per_stage);
@@ -74,7 +74,7 @@ template <int M>
 __device__ __noinline__ bool large_task(const BatchedParams& B, const BatchState& s, int64_t local, float2* smem) {
     if (s.fwd) return large_task_fwd<M>(s, B.ctl, local, smem);
     const G3State S{s.psi, s.N, s.scratch, s.R, s.A, s.U, s.n_batches, s.p1, s.p2, s.p3,
-                    s.ctr, s.ctr + 64, s.ctr + 128};
+                    s.ctr, s.ctr + 64, s.ctr + 128, 0, s.UPW, s.TPT};
     const int64_t per_stage = (int64_t)s.p1 + s.p2 + s.p3;
     const int64_t st = local / per_stage;
     int r = (int)(local % per_stage);

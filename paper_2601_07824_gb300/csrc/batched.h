@@ -20,6 +20,7 @@ struct BatchState {
     // large states
     float2* scratch;           // R x A x 2^(N-1)
     int R, A, U;
+    int UPW, TPT;              // units per pass-1 warp, column tiles per pass-2 task
     int64_t n_batches;
     int p1, p2, p3;
     int64_t n_stage_tasks;     // (n_batches + 2) * (p1 + p2 + p3); forward: (n_batches + 1) * (p1 + p2)

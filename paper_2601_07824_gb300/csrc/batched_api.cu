@@ -59,8 +59,13 @@ Plan make_plan(int count, const void* const* psi, const int* N, void* const* gra
             s.A = A_large;
             s.U = 8 / s.A;
             s.n_batches = dim / s.A;
-            s.p1 = (1 << M) / (s.U * 2);
-            s.p2 = s.A * (1024 >> (13 - M));
+            // 2 units per pass-1 warp, 1 column tile per pass-2 task (larger tasks leave too few
+            // per pipeline stage at N <= 18; measured slower)
+            const int tiles = 1024 >> (13 - M);
+            s.UPW = 2;
+            s.TPT = 1;
+            s.p1 = (1 << M) / (s.U * s.UPW);
+            s.p2 = s.A * tiles / s.TPT;
             s.p3 = s.A * ((1 << M) / 16);
             if (fwd) {
                 s.n_stage_tasks = (s.n_batches + 1) * ((int64_t)s.p1 + s.p2);

@@ -19,12 +19,13 @@ struct DevBuf {
 struct TwoPlan {
     int A, U, R, p1, p2, tiles, triples;  // triples: per-X-string output triples (per_a)
     int UPW, TPT;                         // task shapes: units per pass-1 warp, tiles per pass-2 task
+    int lag;                              // stages between a batch's pass 1 and its pass 2
     size_t scratch_bytes;
 };
 
 // Two-pass task shapes picked by the context's autotuner for one (N, accumulation mode).
 struct TwoShape {
-    int UPW = 0, TPT = 0, R = 0;  // 0: not tuned yet
+    int UPW = 0, TPT = 0, R = 0, lag = 1;  // UPW 0: not tuned yet
     int onepass = 0;              // N = 15: 1 when the one-pass kernel won
 };
 
@@ -63,7 +64,7 @@ bool aligned16(const void* p);
 hadamag_status as_c64(hadamag_ctx_t c, const void* psi, int64_t n, hadamag_dtype dt, cudaStream_t st,
                       const float2** out);
 int sre_mode(double n);
-TwoPlan plan_twopass(int N, int UPW = 2, int TPT = 2, int R = 0);
+TwoPlan plan_twopass(int N, int UPW = 2, int TPT = 2, int R = 0, int lag = 1);
 hadamag_status run_sre(hadamag_ctx_t c, const float2* psi, int N, double n, int64_t count,
                        const int64_t* a_list, int per_a, double* terms, cudaStream_t st, int64_t* nparts);
 hadamag_status launch_twopass_plan(hadamag_ctx_t c, const float2* psi, int N, double n, int mode, const TwoPlan& pl,

@@ -51,7 +51,7 @@ __global__ void __launch_bounds__(256, 2) grad_threepass(GradParams P) {
     extern __shared__ float2 smem[];
     const uint32_t tid = threadIdx.x;
     const G3State S{P.psi, P.N, P.scratch, P.R, P.A, P.U, P.n_batches, P.p1, P.p2, P.p3, P.done1, P.done2, P.done3,
-                    P.a_base};
+                    P.a_base, P.UPW, P.TPT};
     const G3Ctl C{P.status, P.spin_limit, P.wait_bias};
     const int64_t dim = int64_t(1) << P.N;
     const int64_t per_stage = (int64_t)P.p1 + P.p2 + P.p3;

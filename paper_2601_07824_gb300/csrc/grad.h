@@ -24,6 +24,7 @@ struct GradParams {
     float2* gpart;           // per-CTA partial dS_2/dpsi* [grid][2^N] (zeroed before launch)
     double* sums;            // per-CTA [grid][3]: S_2, S_1, 0
     int64_t a_base = 0;      // X-strings a_base .. a_base + A n_batches - 1
+    int UPW = 2, TPT = 1;    // units per pass-1 warp, column tiles per pass-2 task
 };
 
 int grad_onepass_gpc(int N);

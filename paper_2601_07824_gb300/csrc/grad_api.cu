@@ -41,8 +41,13 @@ hadamag_status enqueue_grad_parts(hadamag_ctx_t c, const float2* p, int N, int64
         P.psi = p; P.N = N; P.R = 3; P.A = A; P.U = 8 / A;
         P.n_batches = count / A;
         P.a_base = a0;
-        P.p1 = (1 << M) / (P.U * 2);
-        P.p2 = A * (1024 >> (13 - M));
+        // 2 units per pass-1 warp, 1 column tile per pass-2 task: at these sizes (2^(N-11) units)
+        // larger tasks leave too few per pipeline stage for the grid (measured slower)
+        const int tiles = 1024 >> (13 - M);
+        P.UPW = 2;
+        P.TPT = 1;
+        P.p1 = (1 << M) / (P.U * P.UPW);
+        P.p2 = A * tiles / P.TPT;
         P.p3 = A * ((1 << M) / 16);
         int grid = 0;
         if ((e = grad_threepass_grid(N, c->sm_count, &grid)) != cudaSuccess) return cuda_fail(c, e, "occupancy");

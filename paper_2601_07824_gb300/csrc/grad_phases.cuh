@@ -22,6 +22,8 @@ struct G3State {
     unsigned* done2;
     unsigned* done3;
     int64_t a_base = 0;  // X-string of batch 0, entry 0 (a slice [a_base, a_base + A n_batches))
+    int UPW = 2;         // units per pass-1 warp (even)
+    int TPT = 1;         // column tiles per pass-2 task
 };
 
 struct G3Ctl {
@@ -65,23 +67,28 @@ __device__ __forceinline__ bool g3_pass1(const G3State& S, const G3Ctl& C, int64
     if (g >= S.R && !cta_wait_geq(S.done3 + slot, (unsigned)((g / S.R) * S.p3) + C.wait_bias, C.status, C.spin_limit))
         return false;
     const int a_idx = warp % S.A;
-    const int64_t unit = ((int64_t)r * S.U + warp / S.A) * 2;
+    const int64_t unit = ((int64_t)r * S.U + warp / S.A) * S.UPW;
     const int64_t a = S.a_base + g * S.A + a_idx;
     const int64_t dim = int64_t(1) << S.N;
     // with 8 X-strings per batch (U == 1) the CTA's warps read the same state rows (consecutive
-    // aligned X-strings): stage them once in shared memory (the caller reserves kStageSlots
-    // values after the 8 warps' exchange buffers)
+    // aligned X-strings): stage them once in shared memory, two units at a time (the caller
+    // reserves kStageSlots values after the 8 warps' exchange buffers)
     const int64_t a0 = S.a_base + g * S.A;
     const bool stage = S.U == 1 && a0 < dim;  // CTA-uniform
     float2* rows = smem + 8 * tile_slots(10);
-    if (stage) stage_rows<M>(rows, S.psi, a0, unit);
-    if (a < dim) {
-        float2* sbase = S.scratch + (size_t)slot * S.A * ((size_t)1 << L);
-        float2* sm = smem + warp * tile_slots(10);
+    float2* sbase = S.scratch + (size_t)slot * S.A * ((size_t)1 << L);
+    float2* sm = smem + warp * tile_slots(10);
+    for (int up = 0; up < S.UPW; up += 2) {
+        if (stage) {
+            if (up > 0) __syncthreads();  // every warp is done with the previous rows
+            stage_rows<M>(rows, S.psi, a0, unit + up);
+        }
+        if (a >= dim) continue;
         float2 x[32];
         for (int uu = 0; uu < 2; ++uu) {
-            const PairRows<K1, M> pr(a, unit + uu);
-            float2* dst = sbase + (size_t)a_idx * ((size_t)1 << L) + ((size_t)(unit + uu) << K1);
+            const int64_t un = unit + up + uu;
+            const PairRows<K1, M> pr(a, un);
+            float2* dst = sbase + (size_t)a_idx * ((size_t)1 << L) + ((size_t)un << K1);
             if (stage) {
                 const float2* rw = rows + uu * 2048;
 #pragma unroll
@@ -101,7 +108,8 @@ __device__ __forceinline__ bool g3_pass1(const G3State& S, const G3Ctl& C, int64
     return true;
 }
 
-// ---- pass 2: tile r of batch g; adds 16 sum(R^4+I^4) and 4 sum(R^2+I^2) of each warp's values
+// ---- pass 2: tiles r TPT .. r TPT + TPT - 1 of batch g (S.TPT column tiles per task); adds
+// 16 sum(R^4+I^4) and 4 sum(R^2+I^2) of each warp's values
 // into acc/acc1 of that warp's lane 0 (no CTA barrier for the sums; the caller combines the 8
 // warps at the end).  If s2_atomic is given, lane 0 of every warp also adds its two sums to it
 // before the task's release.
@@ -117,9 +125,9 @@ __device__ __forceinline__ bool g3_pass2(const G3State& S, const G3Ctl& C, int64
     const int slot = (int)(g % S.R);
     if (!cta_wait_geq(S.done1 + slot, (unsigned)((g / S.R + 1) * S.p1) + C.wait_bias, C.status, C.spin_limit))
         return false;
-    const int a_idx = r / TILES, tile = r % TILES;
+    const int a_idx = r / (TILES / S.TPT);
     const int64_t a = S.a_base + g * S.A + a_idx;
-    if (a < (int64_t(1) << S.N)) {
+    if (a < (int64_t(1) << S.N)) for (int tile = (r % (TILES / S.TPT)) * S.TPT, te = tile + S.TPT; tile < te; ++tile) {
         float2* src = S.scratch + (size_t)slot * S.A * ((size_t)1 << L) + (size_t)a_idx * ((size_t)1 << L) +
                       (size_t)tile * T;
         float2 x[32];

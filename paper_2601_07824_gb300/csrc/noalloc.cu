@@ -104,6 +104,7 @@ extern "C" hadamag_status hadamag_sre_noalloc(const void* psi_dev, int N, double
     P.U = 8;
     P.UPW = 2;
     P.TPT = 2;
+    P.lag = 1;
     P.a_base = 0;
     P.n_batches = P.count;
     P.p1 = (1 << M) / (P.U * P.UPW);

@@ -71,10 +71,14 @@ constexpr uint32_t kStageSlots = 4u << 10;
 
 // Copies the four state rows that the pair products of X-string a on units unit and unit + 1
 // read (PairRows' row A and row B of each unit, 2^10 values each) into rows[0 .. 4 x 2^10):
-// unit uu's rows at rows + 2048 uu (row A) and + 1024 (row B).  cp.async by the 256 threads of
-// the CTA; every thread returns once the copy has landed (one CTA barrier).
+// unit uu's rows at rows + 2048 uu (row A) and + 1024 (row B).  With perm != 0 row B is stored
+// with its 32-value blocks permuted: staged position (X << 5) | w holds B[((X ^ perm) << 5) | w],
+// so that a far X-string's partner value B[j ^ al] (j = (k << 5) | lane, perm = al >> 5) sits at
+// (k << 5) | (lane ^ (al & 31)).  cp.async by the 256 threads of the CTA; every thread returns
+// once the copy has landed (one CTA barrier).
 template <int M>
-__device__ __forceinline__ void stage_rows(float2* rows, const float2* __restrict__ psi, int64_t a, int64_t unit) {
+__device__ __forceinline__ void stage_rows(float2* rows, const float2* __restrict__ psi, int64_t a, int64_t unit,
+                                           uint32_t perm = 0) {
     int64_t rb[4];
 #pragma unroll
     for (int uu = 0; uu < 2; ++uu) {
@@ -88,7 +92,8 @@ __device__ __forceinline__ void stage_rows(float2* rows, const float2* __restric
 #pragma unroll
     for (int q = 0; q < 8; ++q) {
         const uint32_t off = (tid + 256u * (q & 1)) * 2u;
-        cp_async16(rows + (q >> 1) * 1024u + off, psi + rb[q >> 1] + off);
+        const uint32_t dst = (q >> 1) & 1 ? ((((off >> 5) ^ perm) << 5) | (off & 31u)) : off;
+        cp_async16(rows + (q >> 1) * 1024u + dst, psi + rb[q >> 1] + off);
     }
     cp_async_commit();
     cp_async_wait<0>();

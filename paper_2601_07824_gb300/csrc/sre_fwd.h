@@ -36,6 +36,7 @@ struct TwoPassParams {
     float2* scratch;         // R slots x A X-strings x 2^(N-1) complex values
     int R, A, U;             // slots, X-strings per batch, warps per X-string in pass 1 (A*U = 8 or 1)
     int UPW, TPT;            // units per pass-1 warp (K1 = 10; even), column tiles per pass-2 task
+    int lag;                 // pass 2 of a batch runs `lag` stages after its pass 1 (1 <= lag < R)
     int64_t n_batches;
     int p1, p2;              // pass-1 / pass-2 tasks per batch
     int64_t a_base;          // without a list: X-string of entry i is a_base + i

@@ -134,14 +134,27 @@ __global__ void __launch_bounds__(256, 2) sre_twopass(TwoPassParams P) {
     const int64_t total = P.n_batches * per_stage;
     double accw[3] = {0.0, 0.0, 0.0};  // lane 0 of each warp: FP64 sums of the warp's tiles
 
-    // (stage, kind, index) of a task: stage s runs pass 1 of batch s, then pass 2 of batch s-1.
+    // (batch, kind, index) of a task.  With lag D: the first Dh = min(D, n_batches) stages run
+    // pass 1 of batches 0 .. Dh-1; middle stage s (0 <= s < n_batches - Dh) runs pass 1 of batch
+    // s + Dh, then pass 2 of batch s; the tail runs pass 2 of the last Dh batches.  Every task
+    // waits only on tasks of earlier stages (pass 2 of b on pass 1 of b, D stages before it;
+    // pass 1 of b on pass 2 of b - R, which needs R > D).
+    const int64_t Dh = P.lag < P.n_batches ? P.lag : P.n_batches;
+    const int64_t nm = P.n_batches - Dh;
     auto decode = [&](int64_t task, int64_t& g, int& kind, int& r) {
-        if (task < P.p1) { g = 0; kind = 1; r = (int)task; return; }
-        const int64_t tt = task - P.p1;
-        const int64_t s = 1 + tt / per_stage;
-        const int rr = (int)(tt % per_stage);
-        if (s < P.n_batches && rr < P.p1) { g = s; kind = 1; r = rr; }
-        else { g = s - 1; kind = 2; r = (s < P.n_batches) ? rr - P.p1 : rr; }
+        if (task < Dh * P.p1) { g = task / P.p1; kind = 1; r = (int)(task % P.p1); return; }
+        int64_t tt = task - Dh * P.p1;
+        if (tt < nm * per_stage) {
+            const int64_t s = tt / per_stage;
+            const int rr = (int)(tt % per_stage);
+            if (rr < P.p1) { g = s + Dh; kind = 1; r = rr; }
+            else { g = s; kind = 2; r = rr - P.p1; }
+            return;
+        }
+        tt -= nm * per_stage;
+        g = nm + tt / P.p2;
+        kind = 2;
+        r = (int)(tt % P.p2);
     };
     // counter and target a task waits on (none for pass 1 of the first R batches)
     auto dependency = [&](int64_t g, int kind, const unsigned*& ctr, unsigned& need) {
@@ -204,18 +217,23 @@ __global__ void __launch_bounds__(256, 2) sre_twopass(TwoPassParams P) {
                 int64_t a0 = 0;
                 if (P.U == 1) {
                     // every warp on the same units: rows shared when all X-strings of the batch
-                    // agree in their bits above K1 (always so without a list)
+                    // agree in their bits above 5 (always so without a list: 8 consecutive,
+                    // aligned X-strings)
                     const int64_t i0 = g * P.A;  // < count for every batch
                     a0 = P.a_list ? P.a_list[i0] : P.a_base + i0;
                     stage = a0 >= 0 && a0 < dim;
-                    if (P.a_list) stage = __syncthreads_and(stage && (!valid || (a >> K1) == (a0 >> K1))) != 0;
+                    if (P.a_list) stage = __syncthreads_and(stage && (!valid || (a >> 5) == (a0 >> 5))) != 0;
                 }
+                // far batch (a >= 2^K1): row B staged block-permuted by the batch's bits 5..9 of a,
+                // so both pair-product loads are a per-thread base plus a compile-time offset
+                const bool far = stage && (a0 >> K1) != 0;
+                const uint32_t perm = far ? (uint32_t)((a0 >> 5) & 31) : 0u;
                 float2* sm = smem + sub * tile_slots(10);
                 float2* rows = smem + 8 * tile_slots(10);
                 for (int up = 0; up < P.UPW; up += 2) {  // UPW consecutive units per warp, two at a time
                     if (stage) {
                         if (up > 0) __syncthreads();  // every warp is done with the previous rows
-                        stage_rows<M>(rows, psi, a0, unit + up);
+                        stage_rows<M>(rows, psi, a0, unit + up, perm);
                     }
                     if (!valid) continue;
                     float2 x[32];
@@ -223,7 +241,12 @@ __global__ void __launch_bounds__(256, 2) sre_twopass(TwoPassParams P) {
                         const int64_t un = unit + up + uu;
                         const PairRows<K1, M> pr(a, un);
                         float2* dst = sbase + (size_t)a_idx * ((size_t)1 << L) + ((size_t)un << K1);
-                        if (stage) {
+                        if (far) {
+                            const float2* own = rows + uu * 2048 + lane;
+                            const float2* par = rows + uu * 2048 + 1024 + (lane ^ ((uint32_t)a & 31u));
+#pragma unroll
+                            for (int k = 0; k < 32; ++k) x[k] = conj_mul(par[k << 5], own[k << 5]);
+                        } else if (stage) {
                             const float2* rw = rows + uu * 2048;
 #pragma unroll
                             for (int k = 0; k < 32; ++k) x[k] = pr.value_rows(rw, rw + 1024, a, lane | (k << 5));

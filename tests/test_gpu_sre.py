@@ -207,7 +207,8 @@ def test_autotuned_shape_matches_default_shape(N):
             out[id(c)] = M.value
         shape = tuned.twopass_shape(N, 2.0)
         assert shape[0] in (2, 4) and shape[1] in (2, 4) and shape[2] in (3, 4) and shape[3] == 8, shape
-        assert plain.twopass_shape(N, 2.0) == [0, 0, 0, 0]
+        assert shape[4] in (1, 2) and shape[4] < shape[2], shape
+        assert plain.twopass_shape(N, 2.0) == [0, 0, 0, 0, 0]
         assert abs(out[id(tuned)] - out[id(plain)]) <= 1e-12 * abs(out[id(plain)])
     finally:
         tuned.close()
@@ -233,12 +234,12 @@ def test_N15_one_pass_and_two_pass_splits_vs_oracle(n):
     Mo, lno = oracle.sre(psi_np, n)
     c = Context(0)
     try:
-        for upw, tpt in ((-1, 0), (2, 1), (2, 2), (4, 1), (4, 2)):
-            c.set_twopass_shape(N, n, upw, tpt)
+        for upw, tpt, lag in ((-1, 0, 1), (2, 1, 1), (2, 2, 2), (4, 1, 2), (4, 2, 1), (4, 2, 3)):
+            c.set_twopass_shape(N, n, upw, tpt, 0, lag)
             M, ln = _sre_with(c, psi, N, n)
-            assert abs(M - Mo) <= TOL_M * max(1.0, abs(Mo)), (upw, tpt, M, Mo)
+            assert abs(M - Mo) <= TOL_M * max(1.0, abs(Mo)), (upw, tpt, lag, M, Mo)
             assert abs(ln - lno) <= 1e-6
-            assert c.twopass_shape(N, n) == ([-1] * 4 if upw == -1 else [upw, tpt, 4, 8])
+            assert c.twopass_shape(N, n) == ([-1] * 5 if upw == -1 else [upw, tpt, 4, 8, lag])
         with pytest.raises(Exception):
             c.set_twopass_shape(N, n, 3, 1)
     finally:
