@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-new-rows", action="store_true",
                     help="skip the separate-process timing of the Algorithm 3 / 6, sector and qudit workloads")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--shape", default="",
+                    help="profiling aid: UPW,TPT,R,LAG pins the two-pass task shape (no tuning launches)")
     ap.add_argument("--xstrings", type=int, default=0,
                     help="profiling aid: each step evaluates only the first K X-strings of the "
                          "workload (per-X-string sums) instead of the full M_2")
@@ -310,6 +312,9 @@ def main():
     psi_np, desc = workload_state(N)
     psi = torch.from_numpy(psi_np).to(dev)
     ctx = _lib.context(local)
+    if args.shape:
+        upw, tpt, R, lag = (int(v) for v in args.shape.split(","))
+        ctx.set_twopass_shape(N, 2.0, upw, tpt, R, lag)
     path = {"cudacore": _lib.PATH_CUDACORE, "tensor": _lib.PATH_TENSOR, "auto": _lib.PATH_AUTO}[args.path]
     ctx.set_path(path)
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count

@@ -91,7 +91,9 @@ const char* hadamag_last_error(hadamag_ctx_t ctx);
  * context for a given N >= 16 and n times each candidate shape of the two-pass kernel on a
  * bounded range of X-strings (units per pass-1 warp {2, 4}, column tiles per pass-2 task {2, 4},
  * a lag of 1 or 2 stages between a batch's first and second pass, at N = 20 also 3 or 4 ring
- * slots) and keeps the fastest for that context; at N = 15 it tunes the shared-memory split
+ * slots; where a stage holds few tasks also the lag that puts 1.5 grid rounds of tasks between
+ * the two passes, with lag + 1 slots) and keeps the fastest for that context; at N = 15 it tunes
+ * the shared-memory split
  * itself: the whole 2^14-value transform in one CTA (one pass) against two passes through L2.
  * The batched call tunes its x-batch the same way.  Results agree between shapes up to the
  * order of the FP64 partial sums.  hadamag_set_autotune(ctx, 0) uses the default shapes (no
@@ -104,7 +106,7 @@ hadamag_status hadamag_set_autotune(hadamag_ctx_t ctx, int on);
 hadamag_status hadamag_twopass_shape(hadamag_ctx_t ctx, int N, double n, int* out5);
 /* Pins the shape for (N, n) instead of tuning it: upw units per pass-1 warp (2 or 4 for
  * N <= 20, 2 above), tpt column tiles per pass-2 task (a divisor of the tiles per X-string),
- * R ring slots (2..4, or 0 for the default), lag stages between the two passes of a batch
+ * R ring slots (2..63, or 0 for the default), lag stages between the two passes of a batch
  * (1 <= lag < slots); upw = -1 at N = 15 selects the one-pass kernel.  INVALID_ARG for any other
  * value. */
 hadamag_status hadamag_set_twopass_shape(hadamag_ctx_t ctx, int N, double n, int upw, int tpt, int R, int lag);

@@ -200,7 +200,8 @@ hadamag_status launch_twopass_plan(hadamag_ctx_t c, const float2* psi, int N, do
 // task shape on a bounded range of X-strings (a >= 2^(N-1), the common kind; two launches each,
 // the second timed with CUDA events on the call's stream) and keeps the fastest for the context.
 // Candidates: units per pass-1 warp {2, 4} (K1 = 10) x tiles per pass-2 task {2, 4} x a pass-2
-// lag of 1 or 2 stages, and for N = 20 also 3 or 4 ring slots.  At N = 15 the split itself is tuned: the one-pass kernel (the
+// lag of 1 or 2 stages (for N = 20 also 3 or 4 ring slots) or, where a stage holds few tasks,
+// the lag that puts 1.5 grid rounds of tasks between a batch's two passes.  At N = 15 the split itself is tuned: the one-pass kernel (the
 // whole 2^14-value transform in one CTA's shared memory) against two passes through L2 (10 + 4
 // bits; tiles per pass-2 task {1, 2}).  Under stream capture, or with autotuning off, the
 // defaults run (one pass at N = 15).
@@ -215,6 +216,8 @@ hadamag_status tune_twopass(hadamag_ctx_t c, const float2* psi, int N, double n,
     Cand cands[32];
     int nc = 0;
     const bool k10 = twopass_k1(N) == 10;
+    int grid = 0;
+    if ((e = twopass_max_grid(N, mode, c->sm_count, &grid)) != cudaSuccess) return cuda_fail(c, e, "occupancy");
     if (N == 15) cands[nc++] = {0, 0, 0, 1};
     for (int upw : {2, 4}) {
         if (!k10 && upw != 2) continue;
@@ -227,6 +230,14 @@ hadamag_status tune_twopass(hadamag_ctx_t c, const float2* psi, int N, double n,
                 } else {
                     cands[nc++] = {upw, tpt, 0, lag};
                 }
+            }
+            // and the lag that spaces a batch's two passes 1.5 grid rounds apart (few tasks per
+            // stage at N <= 18), with lag + 1 ring slots within 64 MiB
+            if (k10 && grid > 0) {
+                const TwoPlan q = plan_twopass(N, upw, tpt);
+                const int deep = pipeline_lag((int64_t)q.p1 + q.p2, grid, 1, (size_t)q.A << (N - 1) << 3,
+                                              (size_t)64 << 20);
+                if (deep > 2) cands[nc++] = {upw, tpt, deep + 1, deep};
             }
         }
     }
@@ -418,7 +429,7 @@ extern "C" hadamag_status hadamag_set_twopass_shape(hadamag_ctx_t c, int N, doub
     }
     const bool k10 = twopass_k1(N) == 10;
     if ((k10 ? (upw != 2 && upw != 4) : upw != 2) || tpt < 1 || tpt > twopass_tiles_per_a(N) ||
-        (twopass_tiles_per_a(N) % tpt) || !(R == 0 || (R >= 2 && R <= 4)) || lag < 1 ||
+        (twopass_tiles_per_a(N) % tpt) || !(R == 0 || (R >= 2 && R <= 63)) || lag < 1 ||
         lag >= plan_twopass(N, upw, tpt, R).R)
         return HADAMAG_ERR_INVALID_ARG;
     sh.UPW = upw;

@@ -3,7 +3,7 @@
 // The autotuner picks, per set of state sizes (and gradient on/off), the number of X-strings
 // A that a pass-1 task of a large state covers (the x-batch: 8, 4 or 2), by timing one full
 // launch per candidate on the first uncaptured call and caching the fastest.  The pass-1 width
-// (10 bits) and the small/large split (N <= 14 one CTA per state) are fixed by the kernels.
+// (10 bits) and the small/large split (N <= 14: one-pass chunk items) are fixed by the kernels.
 #include <algorithm>
 #include <cstring>
 #include <map>
@@ -17,9 +17,11 @@ using namespace hm;
 
 namespace {
 
-// Device memory the per-CTA partial gradients of the large states may take (one slot each
-// while they fit).
-constexpr size_t kPartBudget = (size_t)16 << 30;
+// Partial-gradient buffer slots of the large states, taken in turn.  The large states run one
+// after another in the static phase, and at most two adjacent ones are in flight at a time
+// (a CTA starts state k + 1 only after its own tasks of state k, and state k's pass 2 needs
+// every CTA's pass 1 of state k), so state k's pass 3 rarely waits for state k - 2's finalize.
+constexpr int kPartSlots = 2;
 
 struct Plan {
     std::vector<BatchState> st;
@@ -30,13 +32,13 @@ struct Plan {
 };
 
 // Builds the state table (offsets into the context buffers are filled in later).
-Plan make_plan(int count, const void* const* psi, const int* N, void* const* grad, int A_large, bool fwd) {
+Plan make_plan(int count, const void* const* psi, const int* N, void* const* grad, int A_large, bool fwd, int grid) {
     std::vector<int> order(count);
     for (int i = 0; i < count; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
         const bool lx = N[x] >= 15, ly = N[y] >= 15;
-        if (lx != ly) return !lx;  // small states first (one long item each), then large
-        return N[x] > N[y];        // largest first
+        if (lx != ly) return lx;  // large states (the static phase) first, then small ones
+        return N[x] > N[y];       // largest first
     });
     Plan p;
     for (int i : order) {
@@ -44,18 +46,20 @@ Plan make_plan(int count, const void* const* psi, const int* N, void* const* gra
         s.psi = reinterpret_cast<const float2*>(psi[i]);
         s.grad = grad ? reinterpret_cast<float2*>(grad[i]) : nullptr;
         s.N = N[i];
-        s.task_begin = p.total;
+        s.task_begin = p.total;  // small states: tickets (large states run a static schedule)
         s.out_idx = i;
         s.fwd = fwd ? 1 : 0;
         const int64_t dim = int64_t(1) << s.N;
         if (s.N <= 14) {
+            // X-string chunks of about 2^23 Pauli strings each (N = 14: 32, 13: 8, 12: 2, else
+            // 1), at most one per S_2 slot of the state
             s.kind = 0;
-            if (!fwd) p.gsmall_bytes += (size_t)(256 / (1 << (s.N - 6))) * dim * sizeof(float2);
-            p.total += 1;
+            s.n_chunks = (int)std::min<int64_t>(2 * kS2Lanes, std::max<int64_t>(1, (dim * dim) >> 23));
+            if (!fwd) p.gsmall_bytes += (size_t)s.n_chunks * (256 >> (s.N - 6)) * dim * sizeof(float2);
+            p.total += s.n_chunks + (s.n_chunks > 1 ? 1 : 0);
         } else {
             s.kind = 1;
             const int M = s.N - 11;
-            s.R = 3;
             s.A = A_large;
             s.U = 8 / s.A;
             s.n_batches = dim / s.A;
@@ -67,15 +71,19 @@ Plan make_plan(int count, const void* const* psi, const int* N, void* const* gra
             s.p1 = (1 << M) / (s.U * s.UPW);
             s.p2 = s.A * tiles / s.TPT;
             s.p3 = s.A * ((1 << M) / 16);
+            // stages between the passes of a batch (the single-state rule: N = 15: 15, 16: 8,
+            // 17: 4, 18: 2 at A = 8 and two CTAs per SM), ring of 2 lag + 1 slots
+            s.lag = pipeline_lag((int64_t)s.p1 + s.p2 + (fwd ? 0 : s.p3), grid, 2,
+                                 (size_t)s.A * (size_t)(dim / 2) * sizeof(float2), (size_t)96 << 20);
+            s.R = 2 * s.lag + 1;
             if (fwd) {
-                s.n_stage_tasks = (s.n_batches + 1) * ((int64_t)s.p1 + s.p2);
+                s.n_stage_tasks = (s.n_batches + s.lag) * ((int64_t)s.p1 + s.p2);
                 s.n_fin = 1;
             } else {
-                s.n_stage_tasks = (s.n_batches + 2) * ((int64_t)s.p1 + s.p2 + s.p3);
+                s.n_stage_tasks = (s.n_batches + 2 * s.lag) * ((int64_t)s.p1 + s.p2 + s.p3);
                 s.n_fin = (int)std::max<int64_t>(1, dim / 2048);
             }
             p.scratch_bytes += (size_t)s.R * s.A * (size_t)(dim / 2) * sizeof(float2);
-            p.total += s.n_stage_tasks + s.n_fin;
             p.n_large++;
             p.dimmax = std::max(p.dimmax, dim);
         }
@@ -105,24 +113,23 @@ hadamag_status run(hadamag_ctx_t c, int count, const void* const* psi, const int
                    void* const* grad, double* m2, cudaStream_t st, int A_large) {
     hadamag_status s;
     cudaError_t e;
-    Plan p = make_plan(count, psi, N, want_grad ? grad : nullptr, A_large, !want_grad);
-    const int ns = (int)p.st.size();
     int grid = 0;
     if ((e = batched_max_grid(c->sm_count, &grid)) != cudaSuccess) return cuda_fail(c, e, "occupancy");
+    Plan p = make_plan(count, psi, N, want_grad ? grad : nullptr, A_large, !want_grad, grid);
+    const int ns = (int)p.st.size();
     // one device allocation carved into: table | counters | s2 | ticket (buffers below separately)
     const size_t table_bytes = (size_t)ns * sizeof(BatchState);
     const size_t ctr_bytes = (size_t)ns * 256 * sizeof(unsigned);
-    const size_t s2_bytes = (size_t)ns * 2 * sizeof(double);
+    const size_t s2_bytes = (size_t)ns * 2 * kS2Lanes * sizeof(double);
     const size_t meta_bytes = table_bytes + ctr_bytes + s2_bytes + 256;
     if ((s = ensure_buf(c, c->batch_meta, meta_bytes))) return s;
     if ((s = ensure_buf(c, c->scratch, std::max<size_t>(p.scratch_bytes, 256)))) return s;
     if ((s = ensure_buf(c, c->batch_sums, std::max<size_t>(p.gsmall_bytes, 256)))) return s;
-    // partial-gradient buffer slots: one per large state while they fit kPartBudget, else fewer
-    // slots taken in turn (slot = large-state index mod slots)
+    // partial-gradient buffer slots, taken in turn (slot = large-state index mod slots)
     const size_t slot_bytes = (size_t)grid * p.dimmax * sizeof(float2);
     int slots = 0;
     if (p.n_large && want_grad) {
-        slots = (int)std::min<size_t>((size_t)p.n_large, std::max<size_t>(1, kPartBudget / slot_bytes));
+        slots = std::min(p.n_large, kPartSlots);
     }
     const size_t gpart_bytes = slots ? (size_t)slots * slot_bytes : 256;
     if ((s = ensure_buf(c, c->grad_acc, gpart_bytes))) return s;
@@ -145,11 +152,11 @@ hadamag_status run(hadamag_ctx_t c, int count, const void* const* psi, const int
         BatchState& b = p.st[k];
         b.ctr = ctr + (size_t)k * 256;
         b.fin = b.ctr + 192;
-        b.s2 = s2 + 2 * k;
+        b.s2 = s2 + 2 * kS2Lanes * k;
         if (b.kind == 0) {
             if (want_grad) {
                 b.gsmall = (float2*)((char*)c->batch_sums.ptr + goff);
-                goff += (size_t)(256 / (1 << (b.N - 6))) * ((size_t)1 << b.N) * sizeof(float2);
+                goff += (size_t)b.n_chunks * (256 >> (b.N - 6)) * ((size_t)1 << b.N) * sizeof(float2);
             }
         } else {
             b.scratch = (float2*)((char*)c->scratch.ptr + soff);
@@ -176,12 +183,13 @@ hadamag_status run(hadamag_ctx_t c, int count, const void* const* psi, const int
     BatchedParams B{};
     B.states = (const BatchState*)meta;
     B.n_states = ns;
+    B.n_large = p.n_large;
     B.total = p.total;
     B.ticket = ticket;
     B.nparts = grid;
     B.m2_out = m2;
     B.ctl = G3Ctl{(int*)c->status.ptr, c->spin_limit, c->wait_bias};
-    e = launch_batched(B, grid, st);
+    e = launch_batched(B, !want_grad, grid, st);
     c->launches++;
     if (e != cudaSuccess) return cuda_fail(c, e, "batched_kernel");
     return HADAMAG_OK;

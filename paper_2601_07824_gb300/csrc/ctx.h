@@ -23,6 +23,17 @@ struct TwoPlan {
     size_t scratch_bytes;
 };
 
+// Lag (stages) between dependent passes of a persistent staged kernel: the smallest D with
+// D x per_stage >= 1.5 grid tasks, so that a task rarely waits on one that started less than a
+// grid round before it; then lowered until the ring of mult D + 1 slots of slot_bytes fits in
+// max_bytes and in the 64 per-slot counters.  At least 1.
+inline int pipeline_lag(int64_t per_stage, int grid, int mult, size_t slot_bytes, size_t max_bytes) {
+    int64_t D = per_stage > 0 ? (3 * (int64_t)grid + 2 * per_stage - 1) / (2 * per_stage) : 1;
+    if (D < 1) D = 1;
+    while (D > 1 && ((size_t)(mult * D + 1) * slot_bytes > max_bytes || mult * D + 1 > 63)) --D;
+    return (int)D;
+}
+
 // Two-pass task shapes picked by the context's autotuner for one (N, accumulation mode).
 struct TwoShape {
     int UPW = 0, TPT = 0, R = 0, lag = 1;  // UPW 0: not tuned yet

@@ -45,7 +45,8 @@ grad_onepass(const float2* __restrict__ psi, int N, double* __restrict__ sums, f
 }
 
 // ------------------------------------------------------------------------------------------
-// Three-pass persistent kernel (K1 = 10, M = N - 11), 256 threads, two CTAs per SM.
+// Three-pass persistent kernel (K1 = 10, M = N - 11), 256 threads, two CTAs per SM; tasks in
+// the stage order of g3_decode, CTA b taking tasks b, b + grid, ...
 template <int M>
 __global__ void __launch_bounds__(256, 2) grad_threepass(GradParams P) {
     extern __shared__ float2 smem[];
@@ -55,18 +56,13 @@ __global__ void __launch_bounds__(256, 2) grad_threepass(GradParams P) {
     const G3Ctl C{P.status, P.spin_limit, P.wait_bias};
     const int64_t dim = int64_t(1) << P.N;
     const int64_t per_stage = (int64_t)P.p1 + P.p2 + P.p3;
-    const int64_t total = (P.n_batches + 2) * per_stage;
+    const int64_t total = (P.n_batches + 2 * P.lag) * per_stage;
     float2* gp = P.gpart + (size_t)blockIdx.x * dim;
     double acc = 0.0, acc1 = 0.0;
     for (int64_t task = blockIdx.x; task < total; task += gridDim.x) {
-        // stage s: pass 1 of batch s, pass 2 of batch s-1, pass 3 of batch s-2
-        const int64_t s = task / per_stage;
-        int r = (int)(task % per_stage);
-        int kind;
+        int kind, r;
         int64_t g;
-        if (r < P.p1) { kind = 1; g = s; }
-        else if (r < P.p1 + P.p2) { kind = 2; g = s - 1; r -= P.p1; }
-        else { kind = 3; g = s - 2; r -= P.p1 + P.p2; }
+        g3_decode(task, P.p1, P.p2, P.p3, P.lag, kind, g, r);
         if (g < 0 || g >= P.n_batches) continue;  // CTA-uniform
         bool ok;
         if (kind == 1) ok = g3_pass1<M>(S, C, g, r, smem);

@@ -25,6 +25,7 @@ struct GradParams {
     double* sums;            // per-CTA [grid][3]: S_2, S_1, 0
     int64_t a_base = 0;      // X-strings a_base .. a_base + A n_batches - 1
     int UPW = 2, TPT = 1;    // units per pass-1 warp, column tiles per pass-2 task
+    int lag = 1;             // stages between the passes of a batch (R >= 2 lag + 1)
 };
 
 int grad_onepass_gpc(int N);

@@ -38,7 +38,7 @@ hadamag_status enqueue_grad_parts(hadamag_ctx_t c, const float2* p, int N, int64
         const int M = N - 11;
         const size_t per_a = (size_t)dim / 2 * sizeof(float2);
         const int A = 8;  // the 8 pass-1 warps share the state rows of two units (staged once)
-        P.psi = p; P.N = N; P.R = 3; P.A = A; P.U = 8 / A;
+        P.psi = p; P.N = N; P.A = A; P.U = 8 / A;
         P.n_batches = count / A;
         P.a_base = a0;
         // 2 units per pass-1 warp, 1 column tile per pass-2 task: at these sizes (2^(N-11) units)
@@ -51,6 +51,10 @@ hadamag_status enqueue_grad_parts(hadamag_ctx_t c, const float2* p, int N, int64
         P.p3 = A * ((1 << M) / 16);
         int grid = 0;
         if ((e = grad_threepass_grid(N, c->sm_count, &grid)) != cudaSuccess) return cuda_fail(c, e, "occupancy");
+        // stages between the passes of a batch, for a ring of 2 lag + 1 slots within 96 MiB of
+        // L2 (N = 16: 8, 17: 4, 18: 2, 19 and 20: 1 with two CTAs per SM)
+        P.lag = pipeline_lag((int64_t)P.p1 + P.p2 + P.p3, grid, 2, (size_t)A * per_a, (size_t)96 << 20);
+        P.R = 2 * P.lag + 1;
         if ((s = ensure_buf(c, c->scratch, (size_t)P.R * A * per_a))) return s;
         if ((s = ensure_buf(c, c->counters, 3 * 64 * sizeof(unsigned)))) return s;
         if ((s = ensure_buf(c, c->grad_acc, (size_t)grid * dim * sizeof(float2)))) return s;

@@ -26,6 +26,21 @@ struct G3State {
     int TPT = 1;         // column tiles per pass-2 task
 };
 
+// Stage order of the three passes with lag D (ring of R >= 2D + 1 slots): stage s runs pass 1
+// of batch s, pass 2 of batch s - D and pass 3 of batch s - 2D, n_batches + 2D stages of
+// p1 + p2 + p3 tasks.  Every pass reads what the previous one wrote D stages (D x (p1 + p2 + p3)
+// tasks) earlier, so with D = 2 a task rarely waits on one that started less than a grid round
+// before it.  g outside [0, n_batches): nothing to do.
+__host__ __device__ __forceinline__ void g3_decode(int64_t task, int p1, int p2, int p3, int D, int& kind,
+                                                   int64_t& g, int& r) {
+    const int64_t per = (int64_t)p1 + p2 + p3;
+    const int64_t st = task / per;
+    r = (int)(task % per);
+    if (r < p1) { kind = 1; g = st; }
+    else if (r < p1 + p2) { kind = 2; g = st - D; r -= p1; }
+    else { kind = 3; g = st - 2 * D; r -= p1 + p2; }
+}
+
 struct G3Ctl {
     int* status;
     long long spin_limit;
@@ -75,13 +90,17 @@ __device__ __forceinline__ bool g3_pass1(const G3State& S, const G3Ctl& C, int64
     // reserves kStageSlots values after the 8 warps' exchange buffers)
     const int64_t a0 = S.a_base + g * S.A;
     const bool stage = S.U == 1 && a0 < dim;  // CTA-uniform
+    // far batch (a0 >= 2^K1): the partner row is staged block-permuted by bits 5..9 of a0, so
+    // both pair-product loads are a per-thread base plus a compile-time offset
+    const bool far = stage && (a0 >> K1) != 0;
+    const uint32_t perm = far ? (uint32_t)((a0 >> 5) & 31) : 0u;
     float2* rows = smem + 8 * tile_slots(10);
     float2* sbase = S.scratch + (size_t)slot * S.A * ((size_t)1 << L);
     float2* sm = smem + warp * tile_slots(10);
     for (int up = 0; up < S.UPW; up += 2) {
         if (stage) {
             if (up > 0) __syncthreads();  // every warp is done with the previous rows
-            stage_rows<M>(rows, S.psi, a0, unit + up);
+            stage_rows<M>(rows, S.psi, a0, unit + up, perm);
         }
         if (a >= dim) continue;
         float2 x[32];
@@ -89,7 +108,12 @@ __device__ __forceinline__ bool g3_pass1(const G3State& S, const G3Ctl& C, int64
             const int64_t un = unit + up + uu;
             const PairRows<K1, M> pr(a, un);
             float2* dst = sbase + (size_t)a_idx * ((size_t)1 << L) + ((size_t)un << K1);
-            if (stage) {
+            if (far) {
+                const float2* own = rows + uu * 2048 + lane;
+                const float2* par = rows + uu * 2048 + 1024 + (lane ^ ((uint32_t)a & 31u));
+#pragma unroll
+                for (int k = 0; k < 32; ++k) x[k] = conj_mul(par[k << 5], own[k << 5]);
+            } else if (stage) {
                 const float2* rw = rows + uu * 2048;
 #pragma unroll
                 for (int k = 0; k < 32; ++k) x[k] = pr.value_rows(rw, rw + 1024, a, lane | (k << 5));
@@ -108,11 +132,15 @@ __device__ __forceinline__ bool g3_pass1(const G3State& S, const G3Ctl& C, int64
     return true;
 }
 
+// Lanes of a state's [S_2, S_1] accumulator in the batched launch (pass-2 tasks add into lane
+// blockIdx mod kS2Lanes, which keeps the atomics on one address few).
+constexpr int kS2Lanes = 16;
+
 // ---- pass 2: tiles r TPT .. r TPT + TPT - 1 of batch g (S.TPT column tiles per task); adds
 // 16 sum(R^4+I^4) and 4 sum(R^2+I^2) of each warp's values
 // into acc/acc1 of that warp's lane 0 (no CTA barrier for the sums; the caller combines the 8
-// warps at the end).  If s2_atomic is given, lane 0 of every warp also adds its two sums to it
-// before the task's release.
+// warps at the end).  If s2_atomic is given ([kS2Lanes][2] doubles), lane 0 of every warp also
+// adds its two sums to lane (8 blockIdx + warp) mod kS2Lanes of it before the task's release.
 // FWD: forward only (M_2 without the gradient): no cube, back-transform or store.
 template <int M, bool FWD = false>
 __device__ __forceinline__ bool g3_pass2(const G3State& S, const G3Ctl& C, int64_t g, int r, float2* smem,
@@ -168,7 +196,11 @@ __device__ __forceinline__ bool g3_pass2(const G3State& S, const G3Ctl& C, int64
             const double t0 = 16.0 * (double)q, t1 = 4.0 * (double)s1;
             acc += t0;
             acc1 += t1;
-            if (s2_atomic) { atomicAdd(s2_atomic, t0); atomicAdd(s2_atomic + 1, t1); }
+            if (s2_atomic) {
+                double* d = s2_atomic + 2 * ((blockIdx.x * 8u + (tid >> 5)) % kS2Lanes);
+                atomicAdd(d, t0);
+                atomicAdd(d + 1, t1);
+            }
         }
     }
     __syncthreads();

@@ -206,8 +206,10 @@ def test_autotuned_shape_matches_default_shape(N):
                     "hadamag_sre")
             out[id(c)] = M.value
         shape = tuned.twopass_shape(N, 2.0)
-        assert shape[0] in (2, 4) and shape[1] in (2, 4) and shape[2] in (3, 4) and shape[3] == 8, shape
-        assert shape[4] in (1, 2) and shape[4] < shape[2], shape
+        assert shape[0] in (2, 4) and shape[1] in (2, 4) and shape[3] == 8, shape
+        # a lag of 1 or 2 stages in 3 or 4 ring slots, or a deeper lag with lag + 1 slots
+        assert (shape[2] in (3, 4) and shape[4] in (1, 2)) or (shape[4] > 2 and shape[2] == shape[4] + 1), shape
+        assert 1 <= shape[4] < shape[2] <= 63, shape
         assert plain.twopass_shape(N, 2.0) == [0, 0, 0, 0, 0]
         assert abs(out[id(tuned)] - out[id(plain)]) <= 1e-12 * abs(out[id(plain)])
     finally:
@@ -234,12 +236,13 @@ def test_N15_one_pass_and_two_pass_splits_vs_oracle(n):
     Mo, lno = oracle.sre(psi_np, n)
     c = Context(0)
     try:
-        for upw, tpt, lag in ((-1, 0, 1), (2, 1, 1), (2, 2, 2), (4, 1, 2), (4, 2, 1), (4, 2, 3)):
-            c.set_twopass_shape(N, n, upw, tpt, 0, lag)
+        for upw, tpt, R, lag in ((-1, 0, 0, 1), (2, 1, 0, 1), (2, 2, 0, 2), (4, 1, 0, 2), (4, 2, 0, 1), (4, 2, 0, 3),
+                                 (2, 1, 21, 20), (4, 2, 63, 62)):
+            c.set_twopass_shape(N, n, upw, tpt, R, lag)
             M, ln = _sre_with(c, psi, N, n)
-            assert abs(M - Mo) <= TOL_M * max(1.0, abs(Mo)), (upw, tpt, lag, M, Mo)
+            assert abs(M - Mo) <= TOL_M * max(1.0, abs(Mo)), (upw, tpt, R, lag, M, Mo)
             assert abs(ln - lno) <= 1e-6
-            assert c.twopass_shape(N, n) == ([-1] * 5 if upw == -1 else [upw, tpt, 4, 8, lag])
+            assert c.twopass_shape(N, n) == ([-1] * 5 if upw == -1 else [upw, tpt, R or 4, 8, lag])
         with pytest.raises(Exception):
             c.set_twopass_shape(N, n, 3, 1)
     finally:
