@@ -85,9 +85,12 @@ __device__ __noinline__ bool small_finalize(const BatchedParams& B, const BatchS
     return true;
 }
 
-// One stage task (local index `local` in the state's list) of a large state.
+// One stage task (local index `local` in the state's list) of a large state.  prev_ok: this CTA
+// has already seen the previous user of the state's partial-gradient slot finish (its pass-3
+// tasks then skip that wait).
 template <int M, bool FWD>
-__device__ __forceinline__ bool large_task(const BatchedParams& B, const BatchState& s, int64_t local, float2* smem) {
+__device__ __forceinline__ bool large_task(const BatchedParams& B, const BatchState& s, int64_t local, float2* smem,
+                                           bool& prev_ok) {
     if constexpr (FWD) {
         // forward only: stage st = pass 1 of batch st, pass 2 of batch st - lag; a slot is reused
         // once its pass 2 is done (the done3 / p3 fields of the state view point at done2 / p2)
@@ -116,8 +119,10 @@ __device__ __forceinline__ bool large_task(const BatchedParams& B, const BatchSt
             double acc = 0.0, acc1 = 0.0;
             return g3_pass2<M>(S, B.ctl, g, r, smem, acc, acc1, s.s2);
         }
-        // pass 3 writes the shared partials: the previous large state must have released them
-        const unsigned* prev = s.prev_fin;
+        // pass 3 writes the shared partials: the previous large state on the slot must have
+        // released them (waited for once per CTA and state)
+        const unsigned* prev = prev_ok ? nullptr : s.prev_fin;
+        prev_ok = true;
         return g3_pass3<M>(S, B.ctl, g, r, smem, s.gpart + ((size_t)blockIdx.x << s.N), prev,
                            prev ? s.prev_nfin : 0u);
     }
@@ -165,7 +170,7 @@ __device__ __forceinline__ bool finalize_task(const BatchedParams& B, const Batc
     }
     if (threadIdx.x == 0 && f == 0) m2_out[s.out_idx] = -log2(S2 / (double)dim);
     __syncthreads();
-    if (threadIdx.x == 0) { __threadfence(); red_release_add(s.fin, 1u); }
+    if (threadIdx.x == 0) red_release_add(s.fin, 1u);
     return true;
 }
 
@@ -173,8 +178,9 @@ __device__ __forceinline__ bool finalize_task(const BatchedParams& B, const Batc
 // state's stage tasks plus finalize tasks.
 template <int M, bool FWD>
 __device__ __forceinline__ bool run_large(const BatchedParams& B, const BatchState& s, int64_t first, float2* smem) {
+    bool prev_ok = s.prev_fin == nullptr;
     for (int64_t t = first; t < s.n_stage_tasks + s.n_fin; t += gridDim.x) {
-        const bool ok = t < s.n_stage_tasks ? large_task<M, FWD>(B, s, t, smem)
+        const bool ok = t < s.n_stage_tasks ? large_task<M, FWD>(B, s, t, smem, prev_ok)
                                             : finalize_task(B, s, (int)(t - s.n_stage_tasks), B.m2_out);
         if (!ok) return false;
     }

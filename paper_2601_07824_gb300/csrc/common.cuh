@@ -233,7 +233,8 @@ __device__ __forceinline__ void discard_l2_line(const void* p) {
 // Thread 0 spins (bounded) until *ctr >= target; every thread returns whether the launch is
 // still healthy.  On running out of iterations the status word gets ST_TIMEOUT.
 // `seen` is a value of *ctr thread 0 read earlier with a relaxed load (0 if none): when it
-// already meets the target, an acquire fence replaces the polling.
+// already meets the target, an acquire fence replaces the polling, and the status word is not
+// read (a failure elsewhere is seen at the next wait that has to poll).
 __device__ __forceinline__ bool cta_wait_geq(const unsigned* ctr, unsigned target, int* status,
                                              long long limit, unsigned seen = 0) {
     __shared__ int ok;
@@ -241,12 +242,14 @@ __device__ __forceinline__ bool cta_wait_geq(const unsigned* ctr, unsigned targe
         long long it = 0;
         int good = 1;
         if (seen >= target) fence_acquire();
-        else while (ld_acquire(ctr) < target) {
-            if (ld_status(status) != 0) { good = 0; break; }
-            if (++it > limit) { atomicOr(status, ST_TIMEOUT); good = 0; break; }
-            __nanosleep(100);
+        else {
+            while (ld_acquire(ctr) < target) {
+                if (ld_status(status) != 0) { good = 0; break; }
+                if (++it > limit) { atomicOr(status, ST_TIMEOUT); good = 0; break; }
+                __nanosleep(100);
+            }
+            if (good && ld_status(status) != 0) good = 0;
         }
-        if (good && ld_status(status) != 0) good = 0;
         ok = good;
     }
     __syncthreads();

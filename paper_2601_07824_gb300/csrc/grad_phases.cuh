@@ -128,7 +128,7 @@ __device__ __forceinline__ bool g3_pass1(const G3State& S, const G3Ctl& C, int64
         }
     }
     __syncthreads();
-    if (tid == 0) { __threadfence(); red_release_add(S.done1 + slot, 1u); }
+    if (tid == 224) { red_release_add(S.done1 + slot, 1u); }
     return true;
 }
 
@@ -204,7 +204,7 @@ __device__ __forceinline__ bool g3_pass2(const G3State& S, const G3Ctl& C, int64
         }
     }
     __syncthreads();
-    if (tid == 0) { __threadfence(); red_release_add(S.done2 + slot, 1u); }
+    if (tid == 224) { red_release_add(S.done2 + slot, 1u); }
     return true;
 }
 
@@ -257,7 +257,7 @@ __device__ __forceinline__ bool g3_pass3(const G3State& S, const G3Ctl& C, int64
         }
     }
     __syncthreads();
-    if (tid == 0) red_release_add(S.done3 + slot, 1u);
+    if (tid == 224) red_release_add(S.done3 + slot, 1u);
     return true;
 }
 

@@ -276,10 +276,10 @@ __global__ void __launch_bounds__(256, 2) sre_twopass(TwoPassParams P) {
                 }
             }
             __syncthreads();
-            if (tid == 0) {
-                __threadfence();
-                red_release_add(P.done1 + slot, 1u);
-            }
+            // the release orders the whole CTA's writes (after the barrier); a thread of the last
+            // warp issues it, so thread 0 can poll the next task's counter without waiting behind
+            // the release's ordering
+            if (tid == 224) red_release_add(P.done1 + slot, 1u);
         } else {
             // ---- pass 2: transform over the M high bits of z' + reduction ------------------
             const int a_idx = r / (TILES / P.TPT);
@@ -323,7 +323,7 @@ __global__ void __launch_bounds__(256, 2) sre_twopass(TwoPassParams P) {
                 }
             }
             __syncthreads();
-            if (tid == 0) red_release_add(P.done2 + slot, 1u);
+            if (tid == 224) red_release_add(P.done2 + slot, 1u);
         }
     }
     if (!P.per_a) {
