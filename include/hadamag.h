@@ -95,7 +95,9 @@ const char* hadamag_last_error(hadamag_ctx_t ctx);
  * the two passes, with lag + 1 slots) and keeps the fastest for that context; at N = 15 it tunes
  * the shared-memory split
  * itself: the whole 2^14-value transform in one CTA (one pass) against two passes through L2.
- * The batched call tunes its x-batch the same way.  Results agree between shapes up to the
+ * The adjoint (hadamag_sre_grad, N >= 16) tunes its x-batch (8 or 2 X-strings per batch) the
+ * same way, and the batched call its x-batch (8, 4 or 2) per large state size on up to two
+ * states of that size.  Results agree between shapes up to the
  * order of the FP64 partial sums.  hadamag_set_autotune(ctx, 0) uses the default shapes (no
  * tuning launches; one pass at N = 15).  hadamag_twopass_shape reports the shape in use for
  * (N, n): out5 = [units per pass-1 warp, column tiles per pass-2 task, ring slots, X-strings per
@@ -110,6 +112,9 @@ hadamag_status hadamag_twopass_shape(hadamag_ctx_t ctx, int N, double n, int* ou
  * (1 <= lag < slots); upw = -1 at N = 15 selects the one-pass kernel.  INVALID_ARG for any other
  * value. */
 hadamag_status hadamag_set_twopass_shape(hadamag_ctx_t ctx, int N, double n, int upw, int tpt, int R, int lag);
+/* Pins the adjoint's x-batch for N (16 <= N <= 20): A = 8, 4 or 2 X-strings per batch of the
+ * three-pass kernel instead of tuning it.  INVALID_ARG for any other N or A. */
+hadamag_status hadamag_set_grad_xbatch(hadamag_ctx_t ctx, int N, int A);
 
 /*
  * Exact stabilizer Renyi entropy, Eq. (sre) of Sec. 2, evaluated by the per-X-string

@@ -29,6 +29,7 @@ EXPORTS = [
     "hadamag_mana_mixed_qudit", "hadamag_reduced_density_matrix_qudit", "hadamag_set_fp32_powers",
     "hadamag_sre_chunk", "hadamag_sre_slice", "hadamag_sre_combine", "hadamag_sre_grad_slice",
     "hadamag_sre_grad_combine", "hadamag_set_autotune", "hadamag_twopass_shape", "hadamag_set_twopass_shape",
+    "hadamag_set_grad_xbatch",
 ]
 
 
@@ -90,6 +91,7 @@ def load(path: str | None = None):
             "hadamag_set_autotune": [V, I],
             "hadamag_twopass_shape": [V, I, D, ctypes.POINTER(I)],
             "hadamag_set_twopass_shape": [V, I, D, I, I, I, I],
+            "hadamag_set_grad_xbatch": [V, I, I],
             "hadamag_sre_slice": [V, V, I, D, I, L, L, V, V],
             "hadamag_sre_combine": [I, D, PD, L, PD, PD],
             "hadamag_sre_grad_slice": [V, V, I, I, L, L, PD, V, V],
@@ -164,6 +166,10 @@ class Context:
         """Pin the two-pass shape for (N, n) (see hadamag_set_twopass_shape)."""
         self.check(self.lib.hadamag_set_twopass_shape(self.h, int(N), float(n), int(upw), int(tpt), int(R),
                                                       int(lag)), "hadamag_set_twopass_shape")
+
+    def set_grad_xbatch(self, N: int, A: int):
+        """Pin the adjoint's X-strings per batch for N (see hadamag_set_grad_xbatch)."""
+        self.check(self.lib.hadamag_set_grad_xbatch(self.h, int(N), int(A)), "hadamag_set_grad_xbatch")
 
     def set_wait_limit(self, spins: int, bias: int = 0):
         self.check(self.lib.hadamag_set_wait_limit(self.h, int(spins), int(bias)), "hadamag_set_wait_limit")

@@ -1,8 +1,9 @@
 // batched_api.cu -- hadamag_sre_batched: host planning, autotuning and launch of batched.cu.
 //
-// The autotuner picks, per set of state sizes (and gradient on/off), the number of X-strings
-// A that a pass-1 task of a large state covers (the x-batch: 8, 4 or 2), by timing one full
-// launch per candidate on the first uncaptured call and caching the fastest.  The pass-1 width
+// The autotuner picks, per set of state sizes (and gradient on/off) and per large state size N,
+// the number of X-strings A that a pass-1 task covers (the x-batch: 8, 4 or 2), by timing a
+// launch of up to two states of that size per candidate on the first uncaptured call, and
+// caches the choice.  The pass-1 width
 // (10 bits) and the small/large split (N <= 14: one-pass chunk items) are fixed by the kernels.
 #include <algorithm>
 #include <cstring>
@@ -32,7 +33,8 @@ struct Plan {
 };
 
 // Builds the state table (offsets into the context buffers are filled in later).
-Plan make_plan(int count, const void* const* psi, const int* N, void* const* grad, int A_large, bool fwd, int grid) {
+Plan make_plan(int count, const void* const* psi, const int* N, void* const* grad, const int* A_of_N, bool fwd,
+               int grid) {
     std::vector<int> order(count);
     for (int i = 0; i < count; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) {
@@ -60,7 +62,7 @@ Plan make_plan(int count, const void* const* psi, const int* N, void* const* gra
         } else {
             s.kind = 1;
             const int M = s.N - 11;
-            s.A = A_large;
+            s.A = A_of_N[s.N];
             s.U = 8 / s.A;
             s.n_batches = dim / s.A;
             // 2 units per pass-1 warp, 1 column tile per pass-2 task (larger tasks leave too few
@@ -104,18 +106,23 @@ std::string tune_key(int count, const int* N, int want_grad) {
     return k;
 }
 
-std::map<std::string, int>& tune_cache() {
-    static std::map<std::string, int> m;
+// x-batch per state size (index N; only 15..18 are read)
+struct XBatch {
+    int A[19];
+};
+
+std::map<std::string, XBatch>& tune_cache() {
+    static std::map<std::string, XBatch> m;
     return m;
 }
 
 hadamag_status run(hadamag_ctx_t c, int count, const void* const* psi, const int* N, int want_grad,
-                   void* const* grad, double* m2, cudaStream_t st, int A_large) {
+                   void* const* grad, double* m2, cudaStream_t st, const int* A_of_N) {
     hadamag_status s;
     cudaError_t e;
     int grid = 0;
     if ((e = batched_max_grid(c->sm_count, &grid)) != cudaSuccess) return cuda_fail(c, e, "occupancy");
-    Plan p = make_plan(count, psi, N, want_grad ? grad : nullptr, A_large, !want_grad, grid);
+    Plan p = make_plan(count, psi, N, want_grad ? grad : nullptr, A_of_N, !want_grad, grid);
     const int ns = (int)p.st.size();
     // one device allocation carved into: table | counters | s2 | ticket (buffers below separately)
     const size_t table_bytes = (size_t)ns * sizeof(BatchState);
@@ -216,29 +223,44 @@ extern "C" hadamag_status hadamag_sre_batched(hadamag_ctx_t c, int count, const 
     if ((e = cudaStreamIsCapturing(st, &cap)) != cudaSuccess) return cuda_fail(c, e, "capture query");
     const std::string key = tune_key(count, N, want_grad);
     auto it = tune_cache().find(key);
-    int A = 8;
+    XBatch xb;
+    for (int& a : xb.A) a = 8;
     if (it != tune_cache().end()) {
-        A = it->second;
+        xb = it->second;
     } else if (cap == cudaStreamCaptureStatusNone && c->autotune) {
-        // time one launch per candidate x-batch, keep the fastest
-        float best = 1e30f;
+        // per large size N: time a launch of (up to) two of its states for each candidate x-batch,
+        // keep the fastest (the best A differs between sizes: the rows shared at A = 8 against
+        // more, smaller pass-1 tasks at A = 2)
         cudaEvent_t e0, e1;
-        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess) return fail(c, HADAMAG_ERR_CUDA, "events");
-        for (int cand : {8, 4, 2}) {
-            cudaEventRecord(e0, st);
-            hadamag_status s = run(c, count, psi, N, want_grad, grad, m2, st, cand);
-            if (s) { cudaEventDestroy(e0); cudaEventDestroy(e1); return s; }
-            cudaEventRecord(e1, st);
-            if ((e = cudaEventSynchronize(e1)) != cudaSuccess) return cuda_fail(c, e, "tune sync");
-            float ms = 0.f;
-            cudaEventElapsedTime(&ms, e0, e1);
-            if (ms < best) { best = ms; A = cand; }
+        if (cudaEventCreate(&e0) != cudaSuccess) return fail(c, HADAMAG_ERR_CUDA, "events");
+        if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return fail(c, HADAMAG_ERR_CUDA, "events"); }
+        hadamag_status s = HADAMAG_OK;
+        for (int n = 15; n <= 18 && !s; ++n) {
+            std::vector<const void*> sp;
+            std::vector<void*> sg;
+            std::vector<int> sn;
+            for (int i = 0; i < count && sp.size() < 2; ++i)
+                if (N[i] == n) { sp.push_back(psi[i]); sg.push_back(want_grad ? grad[i] : nullptr); sn.push_back(n); }
+            if (sp.empty()) continue;
+            float best = 1e30f;
+            for (int cand : {8, 4, 2}) {
+                XBatch t = xb;
+                t.A[n] = cand;
+                cudaEventRecord(e0, st);
+                if ((s = run(c, (int)sp.size(), sp.data(), sn.data(), want_grad, sg.data(), m2, st, t.A))) break;
+                cudaEventRecord(e1, st);
+                if ((e = cudaEventSynchronize(e1)) != cudaSuccess) { s = cuda_fail(c, e, "tune sync"); break; }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                if (ms < best) { best = ms; xb.A[n] = cand; }
+            }
         }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
-        tune_cache()[key] = A;
+        if (s) return s;
+        tune_cache()[key] = xb;
     }
-    return run(c, count, psi, N, want_grad, grad, m2, st, A);
+    return run(c, count, psi, N, want_grad, grad, m2, st, xb.A);
 }
 
 extern "C" hadamag_status hadamag_batched_status(hadamag_ctx_t c, hadamag_stream_t stream) {

@@ -55,6 +55,7 @@ struct hadamag_ctx_s {
     unsigned wait_bias = 0;
     int autotune = 1;
     hm::TwoShape twopass_shape[25][5];  // [N][mode], filled by the two-pass autotuner
+    int grad_xbatch[25] = {};            // [N]: X-strings per batch of the three-pass adjoint (0: untuned, 8)
     int fp32_powers = 0;  // non-integer n: FP32 powers (mode 4) where n <= 4 and n (N + 2) <= 100
     void* host_table = nullptr;  // pinned copy of the batched state table
     size_t host_table_bytes = 0;

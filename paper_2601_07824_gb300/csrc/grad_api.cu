@@ -1,4 +1,5 @@
 // grad_api.cu -- C ABI entry point for dM_2/dpsi* (adjoint kernels in grad.cu).
+#include <algorithm>
 #include <cmath>
 
 #include "ctx.h"
@@ -37,7 +38,9 @@ hadamag_status enqueue_grad_parts(hadamag_ctx_t c, const float2* p, int N, int64
         GradParams P{};
         const int M = N - 11;
         const size_t per_a = (size_t)dim / 2 * sizeof(float2);
-        const int A = 8;  // the 8 pass-1 warps share the state rows of two units (staged once)
+        // X-strings per batch: 8 (the 8 pass-1 warps share the state rows of two units, staged
+        // once) unless the tuner found 2 faster for this N (more, smaller pass-1 tasks)
+        const int A = c->grad_xbatch[N] ? c->grad_xbatch[N] : 8;
         P.psi = p; P.N = N; P.A = A; P.U = 8 / A;
         P.n_batches = count / A;
         P.a_base = a0;
@@ -77,6 +80,43 @@ hadamag_status enqueue_grad_parts(hadamag_ctx_t c, const float2* p, int N, int64
     return HADAMAG_OK;
 }
 
+// The adjoint's x-batch tuner: on the first uncaptured call for N >= 16 (autotuning on), times
+// the three-pass kernel on 2^13 X-strings (a >= 2^(N-1)) with 8 and with 2 X-strings per batch
+// (two launches each, the second timed with CUDA events) and keeps the faster for the context.
+static hadamag_status tune_grad(hadamag_ctx_t c, const float2* p, int N, cudaStream_t st) {
+    if (N < 16 || c->grad_xbatch[N] || !c->autotune) return HADAMAG_OK;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    cudaError_t e;
+    if ((e = cudaStreamIsCapturing(st, &cap)) != cudaSuccess) return cuda_fail(c, e, "capture query");
+    if (cap != cudaStreamCaptureStatusNone) return HADAMAG_OK;
+    const int64_t dim = int64_t(1) << N, cnt = std::min<int64_t>(dim / 2, int64_t(1) << 13);
+    cudaEvent_t e0, e1;
+    if (cudaEventCreate(&e0) != cudaSuccess) return fail(c, HADAMAG_ERR_CUDA, "events");
+    if (cudaEventCreate(&e1) != cudaSuccess) { cudaEventDestroy(e0); return fail(c, HADAMAG_ERR_CUDA, "events"); }
+    hadamag_status s = HADAMAG_OK;
+    float best = 1e30f;
+    int win = 8;
+    for (int cand : {8, 2}) {
+        c->grad_xbatch[N] = cand;
+        for (int rep = 0; rep < 2 && !s; ++rep) {
+            if (rep == 1) cudaEventRecord(e0, st);
+            int64_t np = 0;
+            s = enqueue_grad_parts(c, p, N, dim / 2, cnt, st, &np);
+            if (rep == 1) cudaEventRecord(e1, st);
+        }
+        if (s) break;
+        if ((e = cudaEventSynchronize(e1)) != cudaSuccess) { s = cuda_fail(c, e, "tune sync"); break; }
+        float ms = 0.f;
+        cudaEventElapsedTime(&ms, e0, e1);
+        if (ms < best) { best = ms; win = cand; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    c->grad_xbatch[N] = s ? 0 : win;
+    if (s) return s;
+    return status_word_now(c, st);
+}
+
 // Enqueues the adjoint: gradient written to grad_out (same dtype as `dt`), and the FP64 sums
 // [S_2, S_1, 0] left in c->res (device).  No host synchronisation.
 hadamag_status enqueue_grad(hadamag_ctx_t c, const float2* p, int N, void* grad_out, bool c128, cudaStream_t st) {
@@ -108,6 +148,7 @@ extern "C" hadamag_status hadamag_sre_grad(hadamag_ctx_t c, const void* psi, int
     if ((s = begin(c, st))) return s;
     const float2* p;
     if ((s = as_c64(c, psi, int64_t(1) << N, dt, st, &p))) return s;
+    if ((s = tune_grad(c, p, N, st))) return s;
     if ((s = enqueue_grad(c, p, N, grad, dt == HADAMAG_C128, st))) return s;
     if ((s = finish(c, (const double*)c->res.ptr, 3, st))) return s;
     const double S2 = c->host_res[0];
@@ -115,5 +156,11 @@ extern "C" hadamag_status hadamag_sre_grad(hadamag_ctx_t c, const void* psi, int
     if (M2 == 0.0) M2 = 0.0;
     *M2_out = M2;
     if (!std::isfinite(M2)) return fail(c, HADAMAG_ERR_NONFINITE, "non-finite S_2");
+    return HADAMAG_OK;
+}
+
+extern "C" hadamag_status hadamag_set_grad_xbatch(hadamag_ctx_t c, int N, int A) {
+    if (!c || N < 16 || N > 20 || (A != 2 && A != 4 && A != 8)) return HADAMAG_ERR_INVALID_ARG;
+    c->grad_xbatch[N] = A;
     return HADAMAG_OK;
 }

@@ -3,6 +3,7 @@ oracle's (brute-force-pinned) forward, and the exact phase/scale identities.
 
 Tolerance: ||g_gpu - g_oracle||_2 <= 1e-5 ||g_oracle||_2 (FP32 transforms, FP32 partial
 gradients over at most 2^N / (number of partials) X-strings each, FP64 reduction)."""
+import ctypes
 import math
 
 import numpy as np
@@ -37,6 +38,38 @@ def test_grad_vs_oracle(N):
     M2o, go = oracle.sre_grad(psi)
     assert abs(M2 - M2o) <= 1e-6 * max(1.0, abs(M2o))
     assert rel(g.cpu().numpy().astype(np.complex128), go) <= 1e-5
+
+
+@pytest.mark.parametrize("N", [16, 17])
+def test_grad_xbatches_agree(N):
+    # the three-pass adjoint with 8, 4 and 2 X-strings per batch (the tuner's candidates): the
+    # same M_2 and gradient up to the order of the partial sums; N = 16 also against the oracle
+    from paper_2601_07824_gb300._lib import Context
+    psi = I.gaussian_state(N, 640 + N, dtype=np.complex64)
+    t = on_dev(psi)
+    c = Context(0)
+    try:
+        out = {}
+        for A in (8, 4, 2):
+            c.set_grad_xbatch(N, A)
+            g = torch.empty_like(t)
+            M = ctypes.c_double()
+            c.check(c.lib.hadamag_sre_grad(c.h, ctypes.c_void_p(t.data_ptr()), N, 0,
+                                           ctypes.byref(M), ctypes.c_void_p(g.data_ptr()),
+                                           ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)),
+                    "hadamag_sre_grad")
+            out[A] = (M.value, g.cpu().numpy().astype(np.complex128))
+        for A in (4, 2):
+            assert abs(out[A][0] - out[8][0]) <= 1e-9 * abs(out[8][0])
+            assert rel(out[A][1], out[8][1]) <= 1e-6
+        if N == 16:
+            M2o, go = oracle.sre_grad(psi)
+            assert abs(out[2][0] - M2o) <= 1e-6 * max(1.0, abs(M2o))
+            assert rel(out[2][1], go) <= 1e-5
+        with pytest.raises(Exception):
+            c.set_grad_xbatch(N, 3)
+    finally:
+        c.close()
 
 
 def test_grad_unnormalised_complex128_vs_oracle():
