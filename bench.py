@@ -667,7 +667,7 @@ def extra_workloads(hm, dev, sm_count, only: str = ""):
     def ti20():
         psi = torch.from_numpy(inputs.brickwork_haar(20, 10, seed=2001, dtype=np.complex64)).to(dev)
         L, n_s, burn = 10, 2000, 200
-        dt, r = timed(lambda: hm.sre_ti(psi, L, n_s, 2002, burn_in=burn), warm=False)
+        dt, r = timed(lambda: hm.sre_ti(psi, L, n_s, 2002, burn_in=burn))
         evals = L * (n_s + burn + 1)
         rate = evals * 2.0 ** 20 / dt
         return {"strings_per_s": rate, "alu_frac": ops_per_string(20) * rate / fp32_peak_ops(sm_count, 2070.0),

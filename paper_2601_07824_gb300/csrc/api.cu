@@ -84,6 +84,9 @@ hadamag_status as_c64(hadamag_ctx_t c, const void* psi, int64_t n, hadamag_dtype
     return HADAMAG_OK;
 }
 
+// X-string counts up to this use the small-task two-pass shape instead of the tuned one.
+constexpr int64_t kFewXstrings = 64;
+
 int sre_mode(double n) { return n == 1.0 ? 1 : n == 2.0 ? 2 : n == 3.0 ? 3 : 0; }
 
 // Two-pass launch shape for N: X-strings per batch A, ring slots R (0: the default), units per
@@ -127,7 +130,7 @@ hadamag_status run_sre(hadamag_ctx_t c, const float2* psi, int N, double n, int6
     if (mode == 0 && c->fp32_powers && n <= 4.0 && n * (N + 2) <= 100.0) mode = 4;
     hadamag_status s;
     cudaError_t e;
-    if (N == 15 && (s = tune_twopass(c, psi, N, n, mode, st))) return s;
+    if (N == 15 && count > kFewXstrings && (s = tune_twopass(c, psi, N, n, mode, st))) return s;
     if (N < 15 || (N == 15 && !c->twopass_shape[N][mode].UPW)) {
         OnepassArgs A{};
         A.psi = psi; A.N = N; A.nq = n; A.count = count; A.a_list = a_list;
@@ -147,6 +150,14 @@ hadamag_status run_sre(hadamag_ctx_t c, const float2* psi, int N, double n, int6
         return HADAMAG_OK;
     }
     if (N > 24) return fail(c, HADAMAG_ERR_UNSUPPORTED, "exact SRE supports N <= 24 (got %d)", N);
+    if (count <= kFewXstrings) {
+        // a few X-strings (Algorithm 3's per-step evaluations): a pinned shape, else the shape
+        // with the most, smallest tasks, so that they spread over the grid (the tuned shapes
+        // are for full sums)
+        const TwoShape& ps = c->twopass_shape[N][mode];
+        const TwoPlan pl = (ps.pinned && ps.UPW) ? plan_twopass(N, ps.UPW, ps.TPT, ps.R, ps.lag) : plan_twopass(N, 2, 1);
+        return launch_twopass_plan(c, psi, N, n, mode, pl, count, a_list, 0, per_a, terms, st, nparts);
+    }
     if ((s = tune_twopass(c, psi, N, n, mode, st))) return s;
     const TwoShape& sh = c->twopass_shape[N][mode];
     TwoPlan pl = sh.UPW ? plan_twopass(N, sh.UPW, sh.TPT, sh.R, sh.lag) : plan_twopass(N);
@@ -159,8 +170,10 @@ hadamag_status launch_twopass_plan(hadamag_ctx_t c, const float2* psi, int N, do
                                    cudaStream_t st, int64_t* nparts) {
     hadamag_status s;
     cudaError_t e;
-    int grid = 0;
-    if ((e = twopass_max_grid(N, mode, c->sm_count, &grid)) != cudaSuccess) return cuda_fail(c, e, "occupancy");
+    int& grid_max = c->twopass_grid[N][mode];  // queried once per context (a host round trip)
+    if (!grid_max && (e = twopass_max_grid(N, mode, c->sm_count, &grid_max)) != cudaSuccess)
+        return cuda_fail(c, e, "occupancy");
+    int grid = grid_max;
     if ((s = ensure_buf(c, c->scratch, pl.scratch_bytes))) return s;
     if ((s = ensure_buf(c, c->counters, 2 * 64 * sizeof(unsigned)))) return s;
     TwoPassParams P{};
@@ -437,6 +450,7 @@ extern "C" hadamag_status hadamag_set_twopass_shape(hadamag_ctx_t c, int N, doub
     sh.R = R;
     sh.lag = lag;
     sh.onepass = 0;
+    sh.pinned = 1;
     return HADAMAG_OK;
 }
 

@@ -38,6 +38,7 @@ inline int pipeline_lag(int64_t per_stage, int grid, int mult, size_t slot_bytes
 struct TwoShape {
     int UPW = 0, TPT = 0, R = 0, lag = 1;  // UPW 0: not tuned yet
     int onepass = 0;              // N = 15: 1 when the one-pass kernel won
+    int pinned = 0;               // set by hadamag_set_twopass_shape (also used for a few X-strings)
 };
 
 }  // namespace hm
@@ -55,6 +56,7 @@ struct hadamag_ctx_s {
     unsigned wait_bias = 0;
     int autotune = 1;
     hm::TwoShape twopass_shape[25][5];  // [N][mode], filled by the two-pass autotuner
+    int twopass_grid[25][5] = {};       // [N][mode]: resident CTAs of the two-pass kernel (0: not queried)
     int grad_xbatch[25] = {};            // [N]: X-strings per batch of the three-pass adjoint (0: untuned, 8)
     int fp32_powers = 0;  // non-integer n: FP32 powers (mode 4) where n <= 4 and n (N + 2) <= 100
     void* host_table = nullptr;  // pinned copy of the batched state table

@@ -78,6 +78,8 @@ inline int twopass_triples_per_a(int N) { return 8 * twopass_tiles_per_a(N); }
 int twopass_k1(int N);
 
 cudaError_t launch_onepass(OnepassArgs& A, int mode, int sm_count, cudaStream_t st);
+// Requires a prior twopass_max_grid(N, mode) on the current device (it sets the kernel's
+// shared-memory limit).
 cudaError_t launch_twopass(const TwoPassParams& P, int mode, int grid, cudaStream_t st);
 cudaError_t twopass_max_grid(int N, int mode, int sm_count, int* grid);
 cudaError_t launch_sum_triples(const double* in, int64_t n, double* out, cudaStream_t st);

@@ -394,11 +394,10 @@ static cudaError_t twopass_prepare(int* occ) {
     return cudaOccupancyMaxActiveBlocksPerMultiprocessor(occ, k, 256, smem);
 }
 
+// The caller has run twopass_max_grid for (N, mode) on this device, which raised the
+// kernel's shared-memory limit (a function attribute that persists on the device).
 template <int K1, int M, int MODE>
 static cudaError_t launch_twopass_t(const TwoPassParams& P, int grid, cudaStream_t st) {
-    int occ = 0;
-    cudaError_t e = twopass_prepare<K1, M, MODE>(&occ);
-    if (e != cudaSuccess) return e;
     sre_twopass<K1, M, MODE><<<grid, 256, twopass_smem<K1, M>(), st>>>(P);
     return cudaGetLastError();
 }
