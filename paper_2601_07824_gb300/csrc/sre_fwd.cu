@@ -26,16 +26,25 @@ __global__ void sum_triples(const double* __restrict__ in, int64_t n, double* __
     if (threadIdx.x == 0) { out[0] = s[0][0]; out[1] = s[1][0]; out[2] = s[2][0]; }
 }
 
-// Per-X-string sums of `tiles` partial triples: out[i] = sum_t in[i][t] (fixed order).
+// Per-X-string sums of `tiles` partial triples: out[i] = sum_t in[i][t].  One warp per X-string:
+// lane l adds t = l, l + 32, ... in order, then a fixed xor-shuffle tree combines the lanes, so
+// the result depends only on the triples (not on the launch or on which calls made them).
 __global__ void sum_tiles(const double* __restrict__ in, int64_t count, int tiles, double* __restrict__ out) {
-    int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= count) return;
+    const int64_t i = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (i >= count) return;  // warp-uniform (blockDim is a multiple of 32)
     double a0 = 0.0, a1 = 0.0, a2 = 0.0;
-    for (int t = 0; t < tiles; ++t) {
+    for (int t = lane; t < tiles; t += 32) {
         const double* p = in + ((size_t)i * tiles + t) * 3;
         a0 += p[0]; a1 += p[1]; a2 += p[2];
     }
-    out[i * 3] = a0; out[i * 3 + 1] = a1; out[i * 3 + 2] = a2;
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, o);
+        a1 += __shfl_xor_sync(0xffffffffu, a1, o);
+        a2 += __shfl_xor_sync(0xffffffffu, a2, o);
+    }
+    if (lane == 0) { out[i * 3] = a0; out[i * 3 + 1] = a1; out[i * 3 + 2] = a2; }
 }
 
 __global__ void c128_to_c64(const double2* __restrict__ in, float2* __restrict__ out, int64_t n) {
@@ -101,7 +110,7 @@ cudaError_t launch_sum_triples(const double* in, int64_t n, double* out, cudaStr
 
 cudaError_t launch_sum_tiles(const double* in, int64_t count, int tiles, double* out, cudaStream_t st) {
     if (count <= 0) return cudaSuccess;
-    sum_tiles<<<(unsigned)((count + 255) / 256), 256, 0, st>>>(in, count, tiles, out);
+    sum_tiles<<<(unsigned)((count * 32 + 255) / 256), 256, 0, st>>>(in, count, tiles, out);
     return cudaGetLastError();
 }
 
