@@ -76,7 +76,7 @@ def workload_state(N: int):
 
 # DRAM bytes (read + write) of one launch of the dominant kernel, from one ncu capture of this
 # exact command on the current kernel (profiles/); absent (null) when no capture matches it.
-TRAFFIC = {(20, 0): 240117637120 + 937505117184}  # sre_twopass<10, 9, 2>, N = 20, one full M2
+TRAFFIC = {(20, 0): 254603761408 + 951125725952}  # sre_twopass<10, 9, 2>, N = 20, one full M2
 
 
 def ops_per_string(N: int) -> int:

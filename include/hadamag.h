@@ -86,8 +86,8 @@ const char* hadamag_status_string(hadamag_status s);
 const char* hadamag_last_error(hadamag_ctx_t ctx);
 
 /*
- * Launch-shape autotuning (not in the paper; the benchmark spec asks for the x-batch and split to be
- * picked by a tuner).  On by default.  With it on, the first uncaptured exact-SRE call of a
+ * Launch-shape autotuning (not in the paper: the x-batch, the shared-memory split and the task
+ * shapes are picked by timing candidates on the device).  On by default.  With it on, the first uncaptured exact-SRE call of a
  * context for a given N >= 16 and n times each candidate shape of the two-pass kernel on a
  * bounded range of X-strings (units per pass-1 warp {2, 4}, column tiles per pass-2 task {2, 4},
  * a lag of 1 or 2 stages between a batch's first and second pass, at N = 20 also 3 or 4 ring
@@ -98,7 +98,9 @@ const char* hadamag_last_error(hadamag_ctx_t ctx);
  * The adjoint (hadamag_sre_grad, N >= 16) tunes its x-batch (8 or 2 X-strings per batch) the
  * same way, and the batched call its x-batch (8, 4 or 2) per large state size on up to two
  * states of that size.  Results agree between shapes up to the
- * order of the FP64 partial sums.  hadamag_set_autotune(ctx, 0) uses the default shapes (no
+ * order of the FP64 partial sums.  Calls over at most 64 X-strings (Algorithm 3's steps, short
+ * lists) use the two-pass shape with the most, smallest tasks (or a pinned one) and do not tune.
+ * hadamag_set_autotune(ctx, 0) uses the default shapes (no
  * tuning launches; one pass at N = 15).  hadamag_twopass_shape reports the shape in use for
  * (N, n): out5 = [units per pass-1 warp, column tiles per pass-2 task, ring slots, X-strings per
  * batch, lag], all 0 before the tuner ran, all -1 when N = 15 runs one pass (15 <= N <= 24;
