@@ -90,7 +90,7 @@ const char* hadamag_last_error(hadamag_ctx_t ctx);
  * shapes are picked by timing candidates on the device).  On by default.  With it on, the first uncaptured exact-SRE call of a
  * context for a given N >= 16 and n times each candidate shape of the two-pass kernel on a
  * bounded range of X-strings (units per pass-1 warp {2, 4}, column tiles per pass-2 task {2, 4},
- * a lag of 1 or 2 stages between a batch's first and second pass, at N = 20 also 3 or 4 ring
+ * a lag of 1 or 2 stages between a batch's first and second pass, at N = 20 also 2, 3 or 4 ring
  * slots; where a stage holds few tasks also the lag that puts 1.5 grid rounds of tasks between
  * the two passes, with lag + 1 slots) and keeps the fastest for that context; at N = 15 it tunes
  * the shared-memory split

@@ -213,7 +213,7 @@ hadamag_status launch_twopass_plan(hadamag_ctx_t c, const float2* psi, int N, do
 // task shape on a bounded range of X-strings (a >= 2^(N-1), the common kind; two launches each,
 // the second timed with CUDA events on the call's stream) and keeps the fastest for the context.
 // Candidates: units per pass-1 warp {2, 4} (K1 = 10) x tiles per pass-2 task {2, 4} x a pass-2
-// lag of 1 or 2 stages (for N = 20 also 3 or 4 ring slots) or, where a stage holds few tasks,
+// lag of 1 or 2 stages (for N = 20 also 2, 3 or 4 ring slots) or, where a stage holds few tasks,
 // the lag that puts 1.5 grid rounds of tasks between a batch's two passes.  At N = 15 the split itself is tuned: the one-pass kernel (the
 // whole 2^14-value transform in one CTA's shared memory) against two passes through L2 (10 + 4
 // bits; tiles per pass-2 task {1, 2}).  Under stream capture, or with autotuning off, the
@@ -239,7 +239,10 @@ hadamag_status tune_twopass(hadamag_ctx_t c, const float2* psi, int N, double n,
             for (int lag : {1, 2}) {
                 if (N == 20) {
                     cands[nc++] = {upw, tpt, 3, lag};
-                    if (lag == 1) cands[nc++] = {upw, tpt, 4, lag};
+                    if (lag == 1) {
+                        cands[nc++] = {upw, tpt, 4, lag};
+                        cands[nc++] = {upw, tpt, 2, lag};  // 64 MiB ring: no scratch write-back
+                    }
                 } else {
                     cands[nc++] = {upw, tpt, 0, lag};
                 }

@@ -207,8 +207,8 @@ def test_autotuned_shape_matches_default_shape(N):
             out[id(c)] = M.value
         shape = tuned.twopass_shape(N, 2.0)
         assert shape[0] in (2, 4) and shape[1] in (2, 4) and shape[3] == 8, shape
-        # a lag of 1 or 2 stages in 3 or 4 ring slots, or a deeper lag with lag + 1 slots
-        assert (shape[2] in (3, 4) and shape[4] in (1, 2)) or (shape[4] > 2 and shape[2] == shape[4] + 1), shape
+        # a lag of 1 or 2 stages in 2 to 4 ring slots, or a deeper lag with lag + 1 slots
+        assert (shape[2] in (2, 3, 4) and shape[4] in (1, 2)) or (shape[4] > 2 and shape[2] == shape[4] + 1), shape
         assert 1 <= shape[4] < shape[2] <= 63, shape
         assert plain.twopass_shape(N, 2.0) == [0, 0, 0, 0, 0]
         assert abs(out[id(tuned)] - out[id(plain)]) <= 1e-12 * abs(out[id(plain)])
