@@ -7,6 +7,7 @@
 #pragma once
 #include "common.cuh"
 #include "pairs.cuh"
+#include "schedule.h"
 #include "sre_fwd.h"
 
 namespace hm {
@@ -25,21 +26,6 @@ struct G3State {
     int UPW = 2;         // units per pass-1 warp (even)
     int TPT = 1;         // column tiles per pass-2 task
 };
-
-// Stage order of the three passes with lag D (ring of R >= 2D + 1 slots): stage s runs pass 1
-// of batch s, pass 2 of batch s - D and pass 3 of batch s - 2D, n_batches + 2D stages of
-// p1 + p2 + p3 tasks.  Every pass reads what the previous one wrote D stages (D x (p1 + p2 + p3)
-// tasks) earlier, so with D = 2 a task rarely waits on one that started less than a grid round
-// before it.  g outside [0, n_batches): nothing to do.
-__host__ __device__ __forceinline__ void g3_decode(int64_t task, int p1, int p2, int p3, int D, int& kind,
-                                                   int64_t& g, int& r) {
-    const int64_t per = (int64_t)p1 + p2 + p3;
-    const int64_t st = task / per;
-    r = (int)(task % per);
-    if (r < p1) { kind = 1; g = st; }
-    else if (r < p1 + p2) { kind = 2; g = st - D; r -= p1; }
-    else { kind = 3; g = st - 2 * D; r -= p1 + p2; }
-}
 
 struct G3Ctl {
     int* status;
@@ -78,8 +64,10 @@ template <int M>
 __device__ __forceinline__ bool g3_pass1(const G3State& S, const G3Ctl& C, int64_t g, int r, float2* smem) {
     constexpr int K1 = 10, L = K1 + M;
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int slot = (int)(g % S.R);
-    if (g >= S.R && !cta_wait_geq(S.done3 + slot, (unsigned)((g / S.R) * S.p3) + C.wait_bias, C.status, C.spin_limit))
+    int slot;
+    unsigned need;
+    if (g3_dependency(g, 1, S.R, S.p1, S.p2, S.p3, slot, need) &&
+        !cta_wait_geq(S.done3 + slot, need + C.wait_bias, C.status, C.spin_limit))
         return false;
     const int a_idx = warp % S.A;
     const int64_t unit = ((int64_t)r * S.U + warp / S.A) * S.UPW;
@@ -150,9 +138,10 @@ __device__ __forceinline__ bool g3_pass2(const G3State& S, const G3Ctl& C, int64
     using S2 = TileSched<13, LOGT, 5>;
     constexpr int SL2 = S2::last_shift();
     const uint32_t tid = threadIdx.x, lane = tid & 31;
-    const int slot = (int)(g % S.R);
-    if (!cta_wait_geq(S.done1 + slot, (unsigned)((g / S.R + 1) * S.p1) + C.wait_bias, C.status, C.spin_limit))
-        return false;
+    int slot;
+    unsigned need;
+    g3_dependency(g, 2, S.R, S.p1, S.p2, S.p3, slot, need);
+    if (!cta_wait_geq(S.done1 + slot, need + C.wait_bias, C.status, C.spin_limit)) return false;
     const int a_idx = r / (TILES / S.TPT);
     const int64_t a = S.a_base + g * S.A + a_idx;
     if (a < (int64_t(1) << S.N)) for (int tile = (r % (TILES / S.TPT)) * S.TPT, te = tile + S.TPT; tile < te; ++tile) {
@@ -215,9 +204,10 @@ __device__ __forceinline__ bool g3_pass3(const G3State& S, const G3Ctl& C, int64
                                          unsigned extra_need = 0) {
     constexpr int K1 = 10, L = K1 + M;
     const uint32_t tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int slot = (int)(g % S.R);
-    if (!cta_wait_geq(S.done2 + slot, (unsigned)((g / S.R + 1) * S.p2) + C.wait_bias, C.status, C.spin_limit))
-        return false;
+    int slot;
+    unsigned need;
+    g3_dependency(g, 3, S.R, S.p1, S.p2, S.p3, slot, need);
+    if (!cta_wait_geq(S.done2 + slot, need + C.wait_bias, C.status, C.spin_limit)) return false;
     if (extra_ctr && !cta_wait_geq(extra_ctr, extra_need + C.wait_bias, C.status, C.spin_limit)) return false;
     constexpr int PER_A = (1 << M) / 16;
     const int a_idx = r / PER_A;

@@ -25,6 +25,7 @@
 #pragma once
 #include "common.cuh"
 #include "pairs.cuh"
+#include "schedule.h"
 #include "sre_fwd.h"
 
 namespace hm {
@@ -134,38 +135,16 @@ __global__ void __launch_bounds__(256, 2) sre_twopass(TwoPassParams P) {
     const int64_t total = P.n_batches * per_stage;
     double accw[3] = {0.0, 0.0, 0.0};  // lane 0 of each warp: FP64 sums of the warp's tiles
 
-    // (batch, kind, index) of a task.  With lag D: the first Dh = min(D, n_batches) stages run
-    // pass 1 of batches 0 .. Dh-1; middle stage s (0 <= s < n_batches - Dh) runs pass 1 of batch
-    // s + Dh, then pass 2 of batch s; the tail runs pass 2 of the last Dh batches.  Every task
-    // waits only on tasks of earlier stages (pass 2 of b on pass 1 of b, D stages before it;
-    // pass 1 of b on pass 2 of b - R, which needs R > D).
-    const int64_t Dh = P.lag < P.n_batches ? P.lag : P.n_batches;
-    const int64_t nm = P.n_batches - Dh;
+    // task order and waits: schedule.h (twopass_decode, twopass_dependency)
     auto decode = [&](int64_t task, int64_t& g, int& kind, int& r) {
-        if (task < Dh * P.p1) { g = task / P.p1; kind = 1; r = (int)(task % P.p1); return; }
-        int64_t tt = task - Dh * P.p1;
-        if (tt < nm * per_stage) {
-            const int64_t s = tt / per_stage;
-            const int rr = (int)(tt % per_stage);
-            if (rr < P.p1) { g = s + Dh; kind = 1; r = rr; }
-            else { g = s; kind = 2; r = rr - P.p1; }
-            return;
-        }
-        tt -= nm * per_stage;
-        g = nm + tt / P.p2;
-        kind = 2;
-        r = (int)(tt % P.p2);
+        twopass_decode(task, P.p1, P.p2, P.n_batches, P.lag, g, kind, r);
     };
     // counter and target a task waits on (none for pass 1 of the first R batches)
     auto dependency = [&](int64_t g, int kind, const unsigned*& ctr, unsigned& need) {
-        const int slot = (int)(g % P.R);
-        if (kind == 1) {
-            ctr = (g >= P.R) ? P.done2 + slot : nullptr;
-            need = (unsigned)((g / P.R) * P.p2) + P.wait_bias;
-        } else {
-            ctr = P.done1 + slot;
-            need = (unsigned)((g / P.R + 1) * P.p1) + P.wait_bias;
-        }
+        int slot;
+        const int which = twopass_dependency(g, kind, P.R, P.p1, P.p2, slot, need);
+        ctr = which == 0 ? nullptr : (which == 1 ? P.done1 : P.done2) + slot;
+        need += P.wait_bias;
     };
 
     unsigned seen = 0;  // thread 0: relaxed read of the next task's counter, one task ahead
