@@ -60,6 +60,13 @@ def test_null_context_is_rejected_without_gpu(lib):
     g = lib.hadamag_create
     g.restype = ctypes.c_int
     assert g(None, 0) == 1
+    # the tuner controls and pins reject a null context (HADAMAG_ERR_INVALID_ARG) too
+    for name, args in (("hadamag_set_autotune", (None, 1)),
+                       ("hadamag_set_grad_xbatch", (None, 17, 2)),
+                       ("hadamag_set_twopass_shape", (None, 18, ctypes.c_double(2.0), 2, 2, 0, 1))):
+        h = getattr(lib, name)
+        h.restype = ctypes.c_int
+        assert h(*args) == 1, name
 
 
 def test_typed_binding_marshals_every_argument_without_gpu():
